@@ -1,0 +1,336 @@
+"""Benchmark: apply a fused, slab-blocked circuit to a full state vector on one GB300.
+
+Default workload (the plain method at scale): a 34-qubit complex64 layered random circuit of
+depth 40 (U3 on every qubit, then CZ on alternating neighbour pairs; 2,020 gates), seeded
+synthetic input standing in for the paper's generated benchmark circuits.  Other workloads:
+--workload qft32_c128 | layered32_c128 | config1.
+
+One step = qs_apply_plan of the whole circuit on the resident state (every plan step: slab
+passes, remaps).  `value` = input gates / device time of the timed steps (CUDA events on the
+state's stream, W warm-up steps first, barrier + synchronize on both sides, max over ranks).
+`e2e` = the same metric through the public API with host inputs: qs_set_basis +
+qs_apply_circuit (host gate list: planning and upload inside the timed region) +
+qs_expect_pauli_sum read back to the host.
+
+--impl reference runs the FP64 CPU oracle on the host cores on a bounded sample of the same
+workload (a smaller state of the same circuit family, scaled by the state size).
+
+Multi-GPU: replicas only (the path has no exchange step on one-GPU machines); each rank runs the
+full workload and value = ranks x gates / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+HBM_NOMINAL_GBS = 8000.0
+WORKLOADS = {
+    "layered34_c64": dict(n=34, dtype="c64", kind="layered", depth=40, seed=1002),
+    "layered32_c128": dict(n=32, dtype="c128", kind="layered", depth=40, seed=1002),
+    "qft32_c128": dict(n=32, dtype="c128", kind="qft", seed=1002),
+    "layered30_c64": dict(n=30, dtype="c64", kind="layered", depth=40, seed=1002),
+    "config1": dict(n=20, dtype="c128", kind="random", ngates=200, seed=1001),
+}
+
+
+def make_circuit(w, n=None):
+    from paper_2406_14084_gb300 import workloads as W
+
+    n = n or w["n"]
+    if w["kind"] == "layered":
+        return W.layered(n, w["depth"], w["seed"]), 0
+    if w["kind"] == "qft":
+        return W.qft(n), W.random_basis(n, w["seed"])
+    return W.random_circuit(n, w["ngates"], w["seed"]), 0
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return {"hbm_gbs": d.get("hbm_gbs"), "source": "of measured"}
+    return {"hbm_gbs": 6800.0, "source": "of fallback"}
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                smax.append(float(f[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ----------------------------------------------------------------------------- CPU oracle leg
+
+def oracle_sample(w, budget_s: float = 15.0):
+    """Time the FP64 oracle on a smaller state of the same circuit family; return gates/s
+    scaled to the full state size (work per gate is proportional to 2^n)."""
+    import numpy as np
+
+    import oracle
+
+    n_full = w["n"]
+    n_s = min(n_full, 25)
+    gates, x0 = make_circuit(w, n_s)
+    state = oracle.basis_state(n_s, x0 & ((1 << n_s) - 1))
+    oracle.apply_circuit(n_s, gates[:2], state)  # warm
+    done, t0 = 0, time.perf_counter()
+    i = 0
+    while time.perf_counter() - t0 < budget_s and i < len(gates):
+        chunk = gates[i:i + 8]
+        oracle.apply_circuit(n_s, chunk, state)
+        i += len(chunk)
+        done += len(chunk)
+    dt = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    rate = done / dt * (2.0 ** (n_s - n_full))
+    return {"value": rate, "unit": "gates/s", "cores": cores, "kind": "oracle",
+            "sample": f"first {done} gates of the same circuit family on a {n_s}-qubit complex128 "
+                      f"state in {dt:.1f} s, gates/s scaled by 2^({n_s}-{n_full})"}
+
+
+# ----------------------------------------------------------------------------- GPU leg
+
+def run_gpu(args, w, ws, rank, local):
+    import torch
+
+    from paper_2406_14084_gb300 import qs
+    from paper_2406_14084_gb300 import workloads as W
+
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    n = w["n"]
+    dtype = qs.QS_C64 if w["dtype"] == "c64" else qs.QS_C128
+    amp_bytes = 8 if dtype == qs.QS_C64 else 16
+    gates, x0 = make_circuit(w)
+    opts = qs.options(dtype=dtype)
+    if args.fuse is not None:
+        opts.fuse_width = args.fuse
+    if args.slab_bits:
+        opts.slab_bits = args.slab_bits
+    if args.slab_mode == "remap":
+        opts.slab_mode = qs.QS_SLAB_REMAP
+    if w["kind"] == "random":
+        opts.fuse_width, opts.blocking = 0, 0
+
+    t_plan0 = time.perf_counter()
+    plan = qs.qs_fuse(gates, n, opts)
+    t_plan = time.perf_counter() - t_plan0
+    info = qs.qs_plan_info_get(plan)
+    nsteps = info["passes"] + info["remaps"] + info["unblocked"] + info["tc_gates"]
+
+    stream = torch.cuda.Stream()
+    state = qs.State(n, dtype)
+    qs.qs_set_stream(state.h, stream.cuda_stream)
+    qs.qs_set_basis(state.h, x0)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        qs.qs_apply_plan(state.h, plan)
+    barrier()
+    qs.qs_stats_reset(state.h)
+    qs.qs_set_profiling(state.h, True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        qs.qs_apply_plan(state.h, plan)
+    ev1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    qs.qs_set_profiling(state.h, False)
+    ms = ev0.elapsed_time(ev1)
+    st = qs.qs_stats(state.h)
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_step = ms / args.steps
+    gates_per_s = ws * len(gates) * args.steps / (ms / 1e3)
+    pass_bytes = 2.0 * (1 << n) * amp_bytes
+    passes_per_step = info["passes"] + info["remaps"] + info["unblocked"]
+    eff_gbs = passes_per_step * pass_bytes / (ms_step / 1e3) / 1e9
+    npass_timed = st["passes"] + st["remaps"] + st["unblocked"]
+    dom_ms = (st["pass_ms"] + st["remap_ms"] + st["unblocked_ms"]) / max(1, npass_timed)
+    peaks = measured_peaks()
+    achieved = pass_bytes / (dom_ms / 1e3) / 1e9
+    norm = qs.qs_norm2(state.h)
+
+    # ---- e2e through the public API with host inputs
+    H = W.zz_chain_hamiltonian(n)
+    e2e_steps = max(1, min(args.steps, args.e2e_steps))
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        qs.qs_set_basis(state.h, x0)
+        qs.qs_apply_circuit(state.h, gates, opts)
+        e = qs.qs_expect_pauli_sum(state.h, H)
+    barrier()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    h2d = info["device_bytes"] + 16 * 256 * 3  # plan upload + one Pauli term group
+    e2e = {"value": ws * len(gates) / e2e_s, "unit": "gates/s", "h2d_bytes_per_step": int(h2d),
+           "d2h_bytes_per_step": 16, "expect_H": e.real}
+
+    state.close()
+    qs.qs_plan_destroy(plan)
+    if dist is not None:
+        dist.destroy_process_group()
+    if rank != 0:
+        return None
+    line = {
+        "metric": "gates/s",
+        "value": gates_per_s,
+        "unit": "gates/s",
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_step,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "c64" if dtype == qs.QS_C64 else "c128",
+        "data": "synthetic (seeded generator, paper-shaped circuit)",
+        "config": {"workload": args.workload, "qubits": n, "gates": len(gates),
+                   "state_bytes": (1 << n) * amp_bytes, "l2": "state larger than L2",
+                   "slab_bits": info["slab_bits"], "seg_bits": info["seg_bits"],
+                   "fused_ops": info["ops"], "passes_per_step": info["passes"],
+                   "remaps_per_step": info["remaps"], "unblocked_per_step": info["unblocked"],
+                   "parallelism": f"replicas x{ws}"},
+        "effective_hbm_gbs": eff_gbs,
+        "effective_frac_of_nominal_8tbs": eff_gbs / HBM_NOMINAL_GBS,
+        "plan_s": t_plan,
+        "norm_after": norm,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                     "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                     "kernel": "slab_pass_kernel", "peak_source": peaks["source"],
+                     "avg_launch_ms": dom_ms, "bytes_per_launch": pass_bytes},
+        "clocks": clk,
+        "gpu_launches": args.steps * nsteps,
+        "e2e": e2e,
+    }
+    return line
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="layered34_c64", choices=sorted(WORKLOADS))
+    ap.add_argument("--fuse", type=int, default=None)
+    ap.add_argument("--slab-bits", type=int, default=0)
+    ap.add_argument("--slab-mode", default="gather", choices=["gather", "remap"])
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    args = ap.parse_args()
+    ws, rank, local = dist_env()
+    w = WORKLOADS[args.workload]
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        vals = []
+        for _ in range(args.warmup):
+            oracle_sample(w, budget_s=min(3.0, args.cpu_budget))
+        samples = [oracle_sample(w, budget_s=args.cpu_budget) for _ in range(args.steps)]
+        vals = [s["value"] for s in samples]
+        v = statistics.median(vals)
+        cpu = dict(samples[0])
+        cpu["value"] = v
+        print(json.dumps({
+            "impl": "reference", "metric": "gates/s", "value": v, "unit": "gates/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * args.cpu_budget, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "c128", "data": "synthetic (seeded generator)",
+            "config": {"workload": args.workload, "qubits": w["n"]},
+            "cpu_baseline": cpu,
+            "e2e": {"value": v, "unit": "gates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        }))
+        return
+
+    line = run_gpu(args, w, ws, rank, local)
+    if line is None:
+        return
+    if not args.no_cpu_baseline and ws == 1:
+        line["cpu_baseline"] = oracle_sample(w, budget_s=args.cpu_budget)
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

@@ -24,7 +24,7 @@ _SO = os.path.join(_BUILD, "libqs_oracle.so")
 _lock = threading.Lock()
 _lib = None
 
-MAX_TARGETS = 7
+MAX_TARGETS = 12
 MAX_CONTROLS = 8
 
 KINDS = {

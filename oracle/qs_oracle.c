@@ -54,7 +54,7 @@ int or_gate_matrix(const or_gate *g, double *Uout)
     const double c = cos(th / 2.0), s = sin(th / 2.0);
     const double r = 1.0 / sqrt(2.0);
     int nt = g->nt;
-    if (nt < 1 || nt > OR_MAX_TARGETS)
+    if (nt < 1 || nt > OR_MAX_DENSE)
         return -1;
     int dim = 1 << nt;
     for (int i = 0; i < dim * dim; ++i)
@@ -175,22 +175,17 @@ static int check_qubits(const or_gate *g, int n)
     return 0;
 }
 
-/* Eq. 2/3: for each index i with all target bits 0 and all control bits 1, the 2^k
- * amplitudes a[i + sum_j bit_j(l) 2^{t_j}] (l < 2^k) are replaced by U times them. */
-int or_apply_gate(double *state, int n, const or_gate *g)
+/* Diagonal gate (the D<k> gates of the artifact appendix): the same groups as Eq. 3, but the
+ * matrix is diagonal, so amplitude a[i + off(l)] is multiplied by entry l. */
+static int apply_diag(cplx *a, int n, const or_gate *g)
 {
-    cplx *a = (cplx *)state;
-    if (check_qubits(g, n)) return -1;
+    if (!g->m) return -3;
     const int k = g->nt, dim = 1 << k;
-    cplx *U = (cplx *)malloc(sizeof(cplx) * (size_t)dim * dim);
-    if (!U) return -2;
-    int rc = or_gate_matrix(g, (double *)U);
-    if (rc) { free(U); return rc; }
     uint64_t tmask = 0, cmask = 0;
     for (int j = 0; j < k; ++j) tmask |= 1ull << g->t[j];
     for (int j = 0; j < g->nc; ++j) cmask |= 1ull << g->c[j];
-    /* offset of local index l: sum over its set bits j of 2^{t_j} */
-    uint64_t off[OR_MAX_DIM];
+    uint64_t *off = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)dim);
+    if (!off) return -2;
     for (int l = 0; l < dim; ++l) {
         uint64_t o = 0;
         for (int j = 0; j < k; ++j)
@@ -202,7 +197,45 @@ int or_apply_gate(double *state, int n, const or_gate *g)
     for (int64_t i = 0; i < N; ++i) {
         if ((uint64_t)i & tmask) continue;
         if (((uint64_t)i & cmask) != cmask) continue;
-        cplx v[OR_MAX_DIM], w[OR_MAX_DIM];
+        for (int l = 0; l < dim; ++l) {
+            const cplx d = g->m[2 * l] + I * g->m[2 * l + 1];
+            a[(uint64_t)i | off[l]] *= d;
+        }
+    }
+    free(off);
+    return 0;
+}
+
+/* Eq. 2/3: for each index i with all target bits 0 and all control bits 1, the 2^k
+ * amplitudes a[i + sum_j bit_j(l) 2^{t_j}] (l < 2^k) are replaced by U times them. */
+int or_apply_gate(double *state, int n, const or_gate *g)
+{
+    cplx *a = (cplx *)state;
+    if (check_qubits(g, n)) return -1;
+    const int k = g->nt, dim = 1 << k;
+    if (g->kind == OR_DIAG) return apply_diag(a, n, g);
+    if (k > OR_MAX_DENSE) return -1;
+    cplx *U = (cplx *)malloc(sizeof(cplx) * (size_t)dim * dim);
+    if (!U) return -2;
+    int rc = or_gate_matrix(g, (double *)U);
+    if (rc) { free(U); return rc; }
+    uint64_t tmask = 0, cmask = 0;
+    for (int j = 0; j < k; ++j) tmask |= 1ull << g->t[j];
+    for (int j = 0; j < g->nc; ++j) cmask |= 1ull << g->c[j];
+    /* offset of local index l: sum over its set bits j of 2^{t_j} */
+    uint64_t off[OR_MAX_DENSE_DIM];
+    for (int l = 0; l < dim; ++l) {
+        uint64_t o = 0;
+        for (int j = 0; j < k; ++j)
+            if (l >> j & 1) o |= 1ull << g->t[j];
+        off[l] = o;
+    }
+    const int64_t N = (int64_t)1 << n;
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < N; ++i) {
+        if ((uint64_t)i & tmask) continue;
+        if (((uint64_t)i & cmask) != cmask) continue;
+        cplx v[OR_MAX_DENSE_DIM], w[OR_MAX_DENSE_DIM];
         for (int l = 0; l < dim; ++l) v[l] = a[(uint64_t)i | off[l]];
         for (int r = 0; r < dim; ++r) {
             cplx acc = 0.0;

@@ -32,9 +32,10 @@ enum {
     OR_CX, OR_CZ, OR_CP, OR_SWAP, OR_RZZ, OR_UNITARY, OR_DIAG
 };
 
-#define OR_MAX_TARGETS 7
+#define OR_MAX_TARGETS 12   /* DIAG gates; dense kinds take at most OR_MAX_DENSE targets */
+#define OR_MAX_DENSE 7
 #define OR_MAX_CONTROLS 8
-#define OR_MAX_DIM (1 << OR_MAX_TARGETS)
+#define OR_MAX_DENSE_DIM (1 << OR_MAX_DENSE)
 
 typedef struct {
     int32_t kind;

@@ -1,0 +1,757 @@
+// api.cpp -- the extern "C" boundary of libqs.so (declared in include/qs.h).
+//
+// Every entry point validates its arguments, catches every C++ exception and converts it to
+// a qs_status with a thread-local message.  Host-side fault injection for tests: the
+// environment variable QS_FAULT=alloc|plan|launch makes the matching step fail with its
+// error status before any device work is issued (no GPU fault is ever provoked).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <memory>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "planner.h"
+#include "qs_internal.h"
+
+using namespace qs;
+
+namespace {
+
+thread_local std::string g_err;
+
+qs_status fail(qs_status st, const std::string &msg)
+{
+    g_err = msg;
+    return st;
+}
+
+bool fault(const char *what)
+{
+    const char *f = std::getenv("QS_FAULT");
+    return f && std::strcmp(f, what) == 0;
+}
+
+qs_status cuda_status(cudaError_t e, const char *what)
+{
+    if (e == cudaSuccess) return QS_OK;
+    cudaGetLastError();
+    if (e == cudaErrorMemoryAllocation) return fail(QS_ENOMEM, std::string(what) + ": out of device memory");
+    return fail(QS_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+size_t amp_bytes(qs_dtype dt) { return dt == QS_C64 ? 8 : 16; }
+
+struct DevPlanBuf {
+    void *base = nullptr;
+    DevPass *passes = nullptr;
+    DevOp *ops = nullptr;
+    void *coef = nullptr;
+    int device = -1;
+};
+
+}  // namespace
+
+struct qs_state {
+    int n = 0;
+    qs_dtype dt = QS_C64;
+    void *amp = nullptr;
+    bool owned = false;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    std::vector<int> phys_of;  // logical -> physical
+    double *scratch = nullptr;
+    size_t scratch_bytes = 0;
+    qs_stats_t stats{};
+    // profiling: event pairs recorded around launches, folded into stats on qs_stats()
+    bool profiling = false;
+    struct Timed {
+        cudaEvent_t a, b;
+        int kind;
+    };
+    std::vector<Timed> pending;
+    std::vector<cudaEvent_t> event_pool;
+    cudaEvent_t take_event()
+    {
+        if (!event_pool.empty()) {
+            cudaEvent_t e = event_pool.back();
+            event_pool.pop_back();
+            return e;
+        }
+        cudaEvent_t e = nullptr;
+        cudaEventCreate(&e);
+        return e;
+    }
+    void fold_timings()
+    {
+        if (pending.empty()) return;
+        cudaStreamSynchronize(stream);
+        for (const Timed &t : pending) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, t.a, t.b);
+            switch (t.kind) {
+            case 0: stats.pass_ms += ms; break;
+            case 1: stats.remap_ms += ms; break;
+            case 2: stats.unblocked_ms += ms; break;
+            default: stats.tc_ms += ms; break;
+            }
+            stats.timed_launches++;
+            event_pool.push_back(t.a);
+            event_pool.push_back(t.b);
+        }
+        pending.clear();
+    }
+    ~qs_state()
+    {
+        for (const Timed &t : pending) {
+            cudaEventDestroy(t.a);
+            cudaEventDestroy(t.b);
+        }
+        for (cudaEvent_t e : event_pool) cudaEventDestroy(e);
+    }
+};
+
+struct qs_plan {
+    Plan p;
+    DevPlanBuf dev[2];  // per dtype
+    ~qs_plan()
+    {
+        for (auto &d : dev)
+            if (d.base) cudaFree(d.base);
+    }
+};
+
+namespace {
+
+bool identity_layout(const qs_state *s)
+{
+    for (int q = 0; q < s->n; ++q)
+        if (s->phys_of[q] != q) return false;
+    return true;
+}
+
+qs_status ensure_scratch(qs_state *s, size_t bytes)
+{
+    if (s->scratch_bytes >= bytes) return QS_OK;
+    if (fault("alloc")) return fail(QS_ENOMEM, "injected allocation failure");
+    if (s->scratch) {
+        cudaStreamSynchronize(s->stream);
+        cudaFree(s->scratch);
+        s->scratch = nullptr;
+        s->scratch_bytes = 0;
+    }
+    void *p = nullptr;
+    qs_status st = cuda_status(cudaMalloc(&p, bytes), "scratch allocation");
+    if (st) return st;
+    s->scratch = (double *)p;
+    s->scratch_bytes = bytes;
+    return QS_OK;
+}
+
+qs_status upload(qs_plan *pl, qs_dtype dt)
+{
+    DevPlanBuf &d = pl->dev[dt];
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (d.base && d.device == dev) return QS_OK;
+    if (d.base) {
+        cudaFree(d.base);
+        d.base = nullptr;
+    }
+    const Plan &p = pl->p;
+    const size_t np = std::max<size_t>(1, p.passes.size()), no = std::max<size_t>(1, p.ops.size());
+    const size_t nc = std::max<size_t>(1, p.coef.size());
+    auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+    const size_t o_pass = 0, o_ops = al(np * sizeof(DevPass)), o_coef = o_ops + al(no * sizeof(DevOp));
+    const size_t total = o_coef + al(nc * amp_bytes(dt));
+    std::vector<unsigned char> h(total, 0);
+    if (!p.passes.empty()) std::memcpy(h.data() + o_pass, p.passes.data(), p.passes.size() * sizeof(DevPass));
+    if (!p.ops.empty()) std::memcpy(h.data() + o_ops, p.ops.data(), p.ops.size() * sizeof(DevOp));
+    if (dt == QS_C64) {
+        float *f = reinterpret_cast<float *>(h.data() + o_coef);
+        for (size_t i = 0; i < p.coef.size(); ++i) {
+            f[2 * i] = (float)p.coef[i].real();
+            f[2 * i + 1] = (float)p.coef[i].imag();
+        }
+    } else {
+        double *f = reinterpret_cast<double *>(h.data() + o_coef);
+        for (size_t i = 0; i < p.coef.size(); ++i) {
+            f[2 * i] = p.coef[i].real();
+            f[2 * i + 1] = p.coef[i].imag();
+        }
+    }
+    if (fault("alloc")) return fail(QS_ENOMEM, "injected allocation failure");
+    void *base = nullptr;
+    qs_status st = cuda_status(cudaMalloc(&base, total), "plan upload allocation");
+    if (st) return st;
+    st = cuda_status(cudaMemcpy(base, h.data(), total, cudaMemcpyHostToDevice), "plan upload");
+    if (st) {
+        cudaFree(base);
+        return st;
+    }
+    d.base = base;
+    d.device = dev;
+    d.passes = reinterpret_cast<DevPass *>((char *)base + o_pass);
+    d.ops = reinterpret_cast<DevOp *>((char *)base + o_ops);
+    d.coef = (char *)base + o_coef;
+    return QS_OK;
+}
+
+int ctas_per_sm_for(qs_dtype dt, int b, int lo)
+{
+    const size_t smem = pass_smem_bytes(dt, b, lo) + 1024;
+    int k = (int)((228 * 1024) / smem);
+    if (k < 1) k = 1;
+    if (k > 8) k = 8;
+    return k;
+}
+
+qs_status run_plan(qs_state *s, qs_plan *pl)
+{
+    if (fault("launch")) return fail(QS_ECUDA, "injected launch failure");
+    qs_status st = upload(pl, s->dt);
+    if (st) return st;
+    const DevPlanBuf &d = pl->dev[s->dt];
+    const Plan &p = pl->p;
+    LaunchCtx c{s->amp, s->n, s->dt, (void *)s->stream};
+    char err[256] = {0};
+    const int64_t pass_bytes = int64_t(2) * (int64_t(1) << s->n) * (int64_t)amp_bytes(s->dt);
+    for (const Step &stp : p.steps) {
+        int rc = QS_OK;
+        cudaEvent_t ev0 = nullptr;
+        if (s->profiling) {
+            ev0 = s->take_event();
+            cudaEventRecord(ev0, s->stream);
+        }
+        switch (stp.kind) {
+        case S_PASS:
+        case S_REMAP: {
+            const DevPass &hp = p.passes[stp.index];
+            rc = launch_pass(c, d.passes + stp.index, hp, d.ops, d.coef, 256,
+                             ctas_per_sm_for(s->dt, hp.b, hp.lo), err, sizeof err);
+            if (stp.kind == S_PASS) s->stats.passes++;
+            else s->stats.remaps++;
+            s->stats.bytes_moved += pass_bytes;
+            break;
+        }
+        case S_UNBLOCKED:
+            rc = launch_unblocked(c, d.ops + stp.index, p.ops[stp.index], d.coef, err, sizeof err);
+            s->stats.unblocked++;
+            s->stats.bytes_moved += pass_bytes;
+            break;
+        case S_TC:
+            return fail(QS_EUNSUPPORTED, "tensor-core step in a plan without tensor-core support");
+        }
+        if (s->profiling) {
+            cudaEvent_t ev1 = s->take_event();
+            cudaEventRecord(ev1, s->stream);
+            const int kind = stp.kind == S_PASS ? 0 : stp.kind == S_REMAP ? 1 : stp.kind == S_UNBLOCKED ? 2 : 3;
+            s->pending.push_back({ev0, ev1, kind});
+            if (s->pending.size() > 4096) s->fold_timings();
+        }
+        if (rc) return fail((qs_status)rc, err);
+    }
+    s->stats.plans_applied++;
+    return QS_OK;
+}
+
+qs_status canonicalize_state(qs_state *s)
+{
+    if (identity_layout(s)) return QS_OK;
+    std::unique_ptr<qs_plan> pl(new qs_plan());
+    pl->p.n = s->n;
+    plan_canonicalize(s->n, s->dt, s->phys_of, pl->p);
+    qs_status st = run_plan(s, pl.get());
+    if (st) return st;
+    // plan buffers are freed by the destructor; wait so the free cannot race the kernels
+    cudaStreamSynchronize(s->stream);
+    for (int q = 0; q < s->n; ++q) s->phys_of[q] = q;
+    return QS_OK;
+}
+
+#define QS_GUARD_BEGIN try {
+#define QS_GUARD_END                                                              \
+    }                                                                             \
+    catch (const std::bad_alloc &) { return fail(QS_ENOMEM, "host allocation failed"); } \
+    catch (const std::exception &e) { return fail(QS_EINVAL, e.what()); }         \
+    catch (...) { return fail(QS_EINVAL, "unknown error"); }
+
+}  // namespace
+
+extern "C" {
+
+const char *qs_last_error(void) { return g_err.c_str(); }
+
+const char *qs_version(void) { return "qs-gb300 0.1 (sm_103a)"; }
+
+void qs_options_default(qs_options *o)
+{
+    if (!o) return;
+    std::memset(o, 0, sizeof *o);
+    o->fuse_width = 2;
+    o->blocking = 1;
+    o->slab_bits = 0;
+    o->seg_bits = 0;
+    o->slab_mode = QS_SLAB_GATHER;
+    o->planner = QS_PLANNER_GREEDY;
+    o->tc = QS_TC_OFF;
+    o->tc_width = 6;
+    o->graph = 0;
+    o->diag_bits = 0;
+    o->dtype = QS_C64;
+}
+
+qs_status qs_create_from_buffer(int n, qs_dtype dt, void *dev, void *stream, qs_state **out)
+{
+    QS_GUARD_BEGIN
+    g_err.clear();
+    if (!out) return fail(QS_EINVAL, "out is NULL");
+    if (n < 1 || n > QS_MAX_QUBITS) return fail(QS_EINVAL, "n must be in [1, 36]");
+    if (dt != QS_C64 && dt != QS_C128) return fail(QS_EINVAL, "bad dtype");
+    if (!dev || (reinterpret_cast<uintptr_t>(dev) & 255)) return fail(QS_EINVAL, "buffer must be non-NULL and 256-byte aligned");
+    std::unique_ptr<qs_state> s(new qs_state());
+    s->n = n;
+    s->dt = dt;
+    s->amp = dev;
+    s->owned = false;
+    s->stream = (cudaStream_t)stream;
+    cudaGetDevice(&s->device);
+    s->phys_of.resize(n);
+    for (int q = 0; q < n; ++q) s->phys_of[q] = q;
+    *out = s.release();
+    return QS_OK;
+    QS_GUARD_END
+}
+
+qs_status qs_create(int n, qs_dtype dt, qs_state **out)
+{
+    QS_GUARD_BEGIN
+    g_err.clear();
+    if (!out) return fail(QS_EINVAL, "out is NULL");
+    if (n < 1 || n > QS_MAX_QUBITS) return fail(QS_EINVAL, "n must be in [1, 36]");
+    if (dt != QS_C64 && dt != QS_C128) return fail(QS_EINVAL, "bad dtype");
+    if (fault("alloc")) return fail(QS_ENOMEM, "injected allocation failure");
+    const size_t bytes = (size_t(1) << n) * amp_bytes(dt);
+    void *p = nullptr;
+    qs_status st = cuda_status(cudaMalloc(&p, bytes), "state allocation");
+    if (st) return st;
+    std::unique_ptr<qs_state> s(new qs_state());
+    s->n = n;
+    s->dt = dt;
+    s->amp = p;
+    s->owned = true;
+    s->stream = nullptr;
+    cudaGetDevice(&s->device);
+    s->phys_of.resize(n);
+    for (int q = 0; q < n; ++q) s->phys_of[q] = q;
+    LaunchCtx c{s->amp, n, dt, nullptr};
+    char err[256] = {0};
+    int rc = launch_set_basis(c, 0, err, sizeof err);
+    if (rc) {
+        cudaFree(p);
+        return fail((qs_status)rc, err);
+    }
+    *out = s.release();
+    return QS_OK;
+    QS_GUARD_END
+}
+
+qs_status qs_destroy(qs_state *s)
+{
+    QS_GUARD_BEGIN
+    if (!s) return QS_OK;
+    cudaStreamSynchronize(s->stream);
+    if (s->owned && s->amp) cudaFree(s->amp);
+    if (s->scratch) cudaFree(s->scratch);
+    delete s;
+    return QS_OK;
+    QS_GUARD_END
+}
+
+qs_status qs_set_stream(qs_state *s, void *stream)
+{
+    if (!s) return fail(QS_EINVAL, "state is NULL");
+    s->stream = (cudaStream_t)stream;
+    return QS_OK;
+}
+
+qs_status qs_sync(qs_state *s)
+{
+    if (!s) return fail(QS_EINVAL, "state is NULL");
+    return cuda_status(cudaStreamSynchronize(s->stream), "synchronize");
+}
+
+qs_status qs_set_basis(qs_state *s, uint64_t x)
+{
+    QS_GUARD_BEGIN
+    if (!s) return fail(QS_EINVAL, "state is NULL");
+    if (s->n < 64 && (x >> s->n)) return fail(QS_EINVAL, "basis index out of range");
+    LaunchCtx c{s->amp, s->n, s->dt, (void *)s->stream};
+    char err[256] = {0};
+    int rc = launch_set_basis(c, x, err, sizeof err);
+    if (rc) return fail((qs_status)rc, err);
+    for (int q = 0; q < s->n; ++q) s->phys_of[q] = q;
+    return QS_OK;
+    QS_GUARD_END
+}
+
+qs_status qs_get_buffer(qs_state *s, void **dev, int *phys_of)
+{
+    if (!s) return fail(QS_EINVAL, "state is NULL");
+    if (dev) *dev = s->amp;
+    if (phys_of)
+        for (int q = 0; q < s->n; ++q) phys_of[q] = s->phys_of[q];
+    return QS_OK;
+}
+
+qs_status qs_canonicalize(qs_state *s)
+{
+    QS_GUARD_BEGIN
+    if (!s) return fail(QS_EINVAL, "state is NULL");
+    return canonicalize_state(s);
+    QS_GUARD_END
+}
+
+qs_status qs_copy_to_host(qs_state *s, uint64_t first, uint64_t count, void *host)
+{
+    QS_GUARD_BEGIN
+    if (!s || (!host && count)) return fail(QS_EINVAL, "NULL argument");
+    const uint64_t N = 1ull << s->n;
+    if (first > N || count > N - first) return fail(QS_EINVAL, "range outside the state");
+    qs_status st = canonicalize_state(s);
+    if (st) return st;
+    const size_t ab = amp_bytes(s->dt);
+    st = cuda_status(cudaMemcpyAsync(host, (char *)s->amp + first * ab, count * ab,
+                                     cudaMemcpyDeviceToHost, s->stream),
+                     "copy to host");
+    if (st) return st;
+    return cuda_status(cudaStreamSynchronize(s->stream), "copy to host");
+    QS_GUARD_END
+}
+
+qs_status qs_copy_from_host(qs_state *s, uint64_t first, uint64_t count, const void *host)
+{
+    QS_GUARD_BEGIN
+    if (!s || (!host && count)) return fail(QS_EINVAL, "NULL argument");
+    const uint64_t N = 1ull << s->n;
+    if (first > N || count > N - first) return fail(QS_EINVAL, "range outside the state");
+    qs_status st = canonicalize_state(s);
+    if (st) return st;
+    const size_t ab = amp_bytes(s->dt);
+    st = cuda_status(cudaMemcpyAsync((char *)s->amp + first * ab, host, count * ab,
+                                     cudaMemcpyHostToDevice, s->stream),
+                     "copy from host");
+    if (st) return st;
+    return cuda_status(cudaStreamSynchronize(s->stream), "copy from host");
+    QS_GUARD_END
+}
+
+qs_status qs_fuse(const qs_gate *g, size_t ng, int n, const qs_options *o, qs_plan **out)
+{
+    QS_GUARD_BEGIN
+    g_err.clear();
+    if (!out) return fail(QS_EINVAL, "out is NULL");
+    if (!g && ng) return fail(QS_EINVAL, "gates is NULL");
+    if (n < 1 || n > QS_MAX_QUBITS) return fail(QS_EINVAL, "n must be in [1, 36]");
+    if (fault("plan")) return fail(QS_EINVAL, "injected planning failure");
+    qs_options opt;
+    if (o) opt = *o;
+    else qs_options_default(&opt);
+    if (opt.fuse_width < 0 || opt.fuse_width > 7 || opt.slab_bits < 0 || opt.slab_bits > kMaxSlabBits ||
+        opt.seg_bits < 0 || opt.seg_bits > 8 || (opt.slab_mode != QS_SLAB_GATHER && opt.slab_mode != QS_SLAB_REMAP) ||
+        (opt.tc != QS_TC_OFF && opt.tc != QS_TC_TF32X3 && opt.tc != QS_TC_BF16X3))
+        return fail(QS_EINVAL, "option out of range");
+    std::vector<CGate> cg;
+    std::string err;
+    int rc = canonicalize(g, ng, n, cg, err);
+    if (rc) return fail((qs_status)rc, err);
+    if (opt.dtype != QS_C64 && opt.dtype != QS_C128) return fail(QS_EINVAL, "bad options dtype");
+    std::unique_ptr<qs_plan> pl(new qs_plan());
+    // A plan can be applied to either precision; opt.dtype selects the cost model it is
+    // optimised for (and the slab size, which must fit shared memory at apply time).
+    rc = build_plan(cg, n, (qs_dtype)opt.dtype, opt, pl->p, err);
+    if (rc) return fail((qs_status)rc, err);
+    *out = pl.release();
+    return QS_OK;
+    QS_GUARD_END
+}
+
+qs_status qs_plan_destroy(qs_plan *p)
+{
+    QS_GUARD_BEGIN
+    if (p) {
+        cudaDeviceSynchronize();
+        delete p;
+    }
+    return QS_OK;
+    QS_GUARD_END
+}
+
+qs_status qs_plan_info_get(const qs_plan *p, qs_plan_info *out)
+{
+    if (!p || !out) return fail(QS_EINVAL, "NULL argument");
+    std::memset(out, 0, sizeof *out);
+    out->n = p->p.n;
+    for (const Step &s : p->p.steps) {
+        if (s.kind == S_PASS) out->passes++;
+        else if (s.kind == S_REMAP) out->remaps++;
+        else if (s.kind == S_UNBLOCKED) out->unblocked++;
+        else if (s.kind == S_TC) out->tc_gates++;
+    }
+    out->ops = p->p.fused_ops;
+    out->input_gates = p->p.input_gates;
+    out->slab_bits = p->p.slab_bits;
+    out->seg_bits = p->p.seg_bits;
+    out->flops_per_amp = p->p.flops_per_amp;
+    out->device_bytes = (int64_t)(p->p.passes.size() * sizeof(DevPass) + p->p.ops.size() * sizeof(DevOp) +
+                                  p->p.coef.size() * 16);
+    return QS_OK;
+}
+
+qs_status qs_plan_dump(const qs_plan *pl, char *buf, size_t cap, size_t *needed)
+{
+    QS_GUARD_BEGIN
+    if (!pl) return fail(QS_EINVAL, "plan is NULL");
+    const Plan &p = pl->p;
+    std::string out;
+    char tmp[64];
+    auto num = [&](long long v) {
+        snprintf(tmp, sizeof tmp, " %lld", v);
+        out += tmp;
+    };
+    auto cnum = [&](const cd &v) {
+        snprintf(tmp, sizeof tmp, " %.17g %.17g", v.real(), v.imag());
+        out += tmp;
+    };
+    out += "N";
+    num(p.n);
+    out += "\n";
+    auto dump_op = [&](const DevOp &op, const int *phys_of_local, bool unblocked) {
+        auto P = [&](int l) { return unblocked ? l : phys_of_local[l]; };
+        static const char *names[] = {"DENSE", "DIAG", "PERMX", "SWAP", "PHASE"};
+        out += "OP ";
+        out += names[op.type];
+        const int kt = op.type == OP_DIAG ? op.k + op.nout : op.type == OP_PERMX ? 1 : op.type == OP_SWAP ? 2 : op.k;
+        num(kt);
+        out += " t";
+        if (op.type == OP_DIAG) {
+            for (int j = 0; j < op.k; ++j) num(P(op.t[j]));
+            for (int j = 0; j < op.nout; ++j) num(op.outpos[j]);
+        } else {
+            for (int j = 0; j < kt; ++j) num(P(op.t[j]));
+        }
+        out += " c";
+        for (int l = 0; l < 64; ++l)
+            if (op.cmask >> l & 1) num(P(l));
+        for (int l = 0; l < 64; ++l)
+            if (op.ocmask >> l & 1) num(l);
+        if (op.type == OP_DENSE || op.type == OP_DIAG) {
+            out += " m";
+            const size_t cnt = op.type == OP_DENSE ? (size_t(1) << (2 * kt)) : (size_t(1) << kt);
+            for (size_t e = 0; e < cnt; ++e) cnum(p.coef[op.mat + e]);
+        }
+        out += "\n";
+    };
+    for (const Step &s : p.steps) {
+        if (s.kind == S_UNBLOCKED) {
+            out += "UNBLOCKED\n";
+            dump_op(p.ops[s.index], nullptr, true);
+        } else if (s.kind == S_PASS || s.kind == S_REMAP) {
+            const DevPass &P = p.passes[s.index];
+            int phys_of_local[32];
+            for (int l = 0; l < P.lo; ++l) phys_of_local[l] = l;
+            for (int j = 0; j < P.nhi; ++j) phys_of_local[P.lo + j] = P.hipos[j];
+            if (s.kind == S_REMAP) {
+                std::vector<int> A, B;
+                for (int l = 0; l < P.b; ++l)
+                    if (P.perm[l] > l) {
+                        A.push_back(phys_of_local[l]);
+                        B.push_back(phys_of_local[P.perm[l]]);
+                    }
+                out += "REMAP";
+                num((long long)A.size());
+                for (int a : A) num(a);
+                for (int b : B) num(b);
+                out += "\n";
+                continue;
+            }
+            out += "PASS";
+            num(P.b);
+            num(P.lo);
+            for (int j = 0; j < P.nhi; ++j) num(P.hipos[j]);
+            out += "\n";
+            for (int o = P.op_begin; o < P.op_end; ++o) dump_op(p.ops[o], phys_of_local, false);
+        }
+    }
+    out += "LAYOUT";
+    for (int q = 0; q < p.n; ++q) num(p.final_phys_of.empty() ? q : p.final_phys_of[q]);
+    out += "\n";
+    if (needed) *needed = out.size() + 1;
+    if (buf && cap) {
+        const size_t m = std::min(cap - 1, out.size());
+        std::memcpy(buf, out.data(), m);
+        buf[m] = 0;
+    }
+    return QS_OK;
+    QS_GUARD_END
+}
+
+qs_status qs_apply_plan(qs_state *s, const qs_plan *p)
+{
+    QS_GUARD_BEGIN
+    if (!s || !p) return fail(QS_EINVAL, "NULL argument");
+    if (p->p.n != s->n) return fail(QS_EINVAL, "plan and state have different qubit counts");
+    const int bmax = max_slab_bits(s->dt);
+    for (const DevPass &ps : p->p.passes)
+        if (ps.b > bmax) return fail(QS_EINVAL, "plan slab too large for this dtype");
+    qs_status st = canonicalize_state(s);
+    if (st) return st;
+    st = run_plan(s, const_cast<qs_plan *>(p));
+    if (st) return st;
+    s->phys_of = p->p.final_phys_of;
+    return QS_OK;
+    QS_GUARD_END
+}
+
+qs_status qs_apply_circuit(qs_state *s, const qs_gate *g, size_t ng, const qs_options *o)
+{
+    QS_GUARD_BEGIN
+    if (!s) return fail(QS_EINVAL, "state is NULL");
+    qs_options opt;
+    if (o) opt = *o;
+    else qs_options_default(&opt);
+    opt.dtype = s->dt;
+    qs_plan *p = nullptr;
+    qs_status st = qs_fuse(g, ng, s->n, &opt, &p);
+    if (st) return st;
+    st = qs_apply_plan(s, p);
+    cudaStreamSynchronize(s->stream);
+    delete p;
+    return st;
+    QS_GUARD_END
+}
+
+qs_status qs_remap(qs_state *s, int k, const int *A, const int *B)
+{
+    QS_GUARD_BEGIN
+    if (!s || (k > 0 && (!A || !B)) || k < 0) return fail(QS_EINVAL, "bad argument");
+    std::vector<int> a(A, A + k), b(B, B + k);
+    std::unique_ptr<qs_plan> pl(new qs_plan());
+    pl->p.n = s->n;
+    std::string err;
+    int rc = plan_remap(s->n, s->dt, a, b, pl->p, err);
+    if (rc) return fail((qs_status)rc, err);
+    qs_status st = run_plan(s, pl.get());
+    if (st) return st;
+    cudaStreamSynchronize(s->stream);
+    std::vector<int> logi(s->n);
+    for (int q = 0; q < s->n; ++q) logi[s->phys_of[q]] = q;
+    for (int j = 0; j < k; ++j) std::swap(logi[a[j]], logi[b[j]]);
+    for (int p = 0; p < s->n; ++p) s->phys_of[logi[p]] = p;
+    return QS_OK;
+    QS_GUARD_END
+}
+
+qs_status qs_norm2(qs_state *s, double *host_out)
+{
+    QS_GUARD_BEGIN
+    if (!s || !host_out) return fail(QS_EINVAL, "NULL argument");
+    qs_status st = ensure_scratch(s, reduce_scratch_bytes());
+    if (st) return st;
+    LaunchCtx c{s->amp, s->n, s->dt, (void *)s->stream};
+    char err[256] = {0};
+    int rc = launch_norm2(c, s->scratch, host_out, err, sizeof err);
+    return rc ? fail((qs_status)rc, err) : QS_OK;
+    QS_GUARD_END
+}
+
+qs_status qs_probs(qs_state *s, const int *qubits, int nq, double *host_out)
+{
+    QS_GUARD_BEGIN
+    if (!s || !host_out || (nq > 0 && !qubits)) return fail(QS_EINVAL, "NULL argument");
+    if (nq < 0 || nq > 24 || nq > s->n) return fail(QS_EINVAL, "nq must be in [0, min(24, n)]");
+    uint64_t seen = 0;
+    std::vector<int> phys(nq > 0 ? nq : 1);
+    for (int j = 0; j < nq; ++j) {
+        const int q = qubits[j];
+        if (q < 0 || q >= s->n || (seen >> q & 1)) return fail(QS_EINVAL, "qubit out of range or repeated");
+        seen |= 1ull << q;
+        phys[j] = s->phys_of[q];
+    }
+    qs_status st = ensure_scratch(s, std::max(reduce_scratch_bytes(), (size_t(1) << nq) * sizeof(double)));
+    if (st) return st;
+    LaunchCtx c{s->amp, s->n, s->dt, (void *)s->stream};
+    char err[256] = {0};
+    int rc = launch_probs(c, phys.data(), nq, s->scratch, s->scratch_bytes, host_out, err, sizeof err);
+    return rc ? fail((qs_status)rc, err) : QS_OK;
+    QS_GUARD_END
+}
+
+qs_status qs_expect_pauli_sum(qs_state *s, const qs_pauli_term *terms, size_t nterms, double *host_out)
+{
+    QS_GUARD_BEGIN
+    if (!s || !host_out || (nterms && !terms)) return fail(QS_EINVAL, "NULL argument");
+    const uint64_t valid = s->n >= 64 ? ~0ull : ((1ull << s->n) - 1);
+    std::vector<uint64_t> xm(nterms), zm(nterms);
+    std::vector<double> cf(nterms);
+    for (size_t t = 0; t < nterms; ++t) {
+        if ((terms[t].xmask & ~valid) || (terms[t].zmask & ~valid))
+            return fail(QS_EINVAL, "Pauli mask has bits beyond n");
+        if (!std::isfinite(terms[t].coeff)) return fail(QS_EINVAL, "non-finite coefficient");
+        uint64_t x = 0, z = 0;
+        for (int q = 0; q < s->n; ++q) {
+            if (terms[t].xmask >> q & 1) x |= 1ull << s->phys_of[q];
+            if (terms[t].zmask >> q & 1) z |= 1ull << s->phys_of[q];
+        }
+        xm[t] = x;
+        zm[t] = z;
+        cf[t] = terms[t].coeff;
+    }
+    if (nterms == 0) {
+        host_out[0] = host_out[1] = 0.0;
+        return QS_OK;
+    }
+    qs_status st = ensure_scratch(s, reduce_scratch_bytes());
+    if (st) return st;
+    LaunchCtx c{s->amp, s->n, s->dt, (void *)s->stream};
+    char err[256] = {0};
+    int rc = launch_expect(c, xm.data(), zm.data(), cf.data(), nterms, s->scratch, s->scratch_bytes,
+                           host_out, err, sizeof err);
+    return rc ? fail((qs_status)rc, err) : QS_OK;
+    QS_GUARD_END
+}
+
+qs_status qs_stats(qs_state *s, qs_stats_t *out)
+{
+    QS_GUARD_BEGIN
+    if (!s || !out) return fail(QS_EINVAL, "NULL argument");
+    s->fold_timings();
+    *out = s->stats;
+    return QS_OK;
+    QS_GUARD_END
+}
+
+qs_status qs_stats_reset(qs_state *s)
+{
+    QS_GUARD_BEGIN
+    if (!s) return fail(QS_EINVAL, "NULL argument");
+    s->fold_timings();
+    std::memset(&s->stats, 0, sizeof s->stats);
+    return QS_OK;
+    QS_GUARD_END
+}
+
+qs_status qs_set_profiling(qs_state *s, int on)
+{
+    QS_GUARD_BEGIN
+    if (!s) return fail(QS_EINVAL, "NULL argument");
+    s->profiling = on != 0;
+    return QS_OK;
+    QS_GUARD_END
+}
+
+}  // extern "C"

@@ -1,0 +1,353 @@
+// k_reduce.cu -- readout reductions over the state vector (one read pass each).
+//
+//  * norm2:  sum |a_x|^2
+//  * probs:  marginal probabilities over a set of physical bit positions
+//  * expect: sum_t c_t <psi|P_t|psi> for Pauli strings, grouped by X mask so that one pass
+//            serves every term with the same X mask: P|x> = i^{#Y} (-1)^{popcount(x&z)} |x^xm>.
+//
+// Accumulation: per-thread partial sums (FP64 for complex128; for complex64 at most 32 FP32
+// terms are summed before conversion to FP64), warp-shuffle and shared-memory tree per block,
+// then a second single-block kernel sums the per-block partials in a fixed order, so results
+// are deterministic for a given launch shape.  The per-block partials live in device scratch
+// memory owned by the state.
+#include <cuda_runtime.h>
+
+#include <cstdio>
+#include <vector>
+
+#include "qs_internal.h"
+
+namespace qs {
+namespace {
+
+constexpr int kRedThreads = 256;
+constexpr int kRedBlocksMax = 4096;
+constexpr int kMaxTermsPerGroup = 256;
+
+template <typename R> struct Cx;
+template <> struct Cx<float> { using T = float2; };
+template <> struct Cx<double> { using T = double2; };
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Block-wide sum of two doubles; result valid in thread 0.
+__device__ __forceinline__ void block_sum2(double &a, double &b)
+{
+    __shared__ double sa[32], sb[32];
+    a = warp_sum(a);
+    b = warp_sum(b);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) { sa[w] = a; sb[w] = b; }
+    __syncthreads();
+    if (w == 0) {
+        const int nw = blockDim.x >> 5;
+        a = lane < nw ? sa[lane] : 0.0;
+        b = lane < nw ? sb[lane] : 0.0;
+        a = warp_sum(a);
+        b = warp_sum(b);
+    }
+}
+
+// Each block handles a contiguous range of amplitudes; thread t of the block reads elements
+// t, t + T, ... of that range (coalesced).
+template <typename R>
+__global__ void __launch_bounds__(kRedThreads) norm2_kernel(const typename Cx<R>::T *__restrict__ a,
+                                                            uint64_t N, double *__restrict__ part)
+{
+    const uint64_t per = (N + gridDim.x - 1) / gridDim.x;
+    const uint64_t lo = per * blockIdx.x;
+    const uint64_t hi = lo + per < N ? lo + per : N;
+    double acc = 0.0;
+    if (sizeof(R) == 4) {
+        float f = 0.f;
+        int cnt = 0;
+        for (uint64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+            const auto v = a[i];
+            f = fmaf((float)v.x, (float)v.x, f);
+            f = fmaf((float)v.y, (float)v.y, f);
+            if (++cnt == 32) { acc += (double)f; f = 0.f; cnt = 0; }
+        }
+        acc += (double)f;
+    } else {
+        for (uint64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+            const auto v = a[i];
+            acc = fma((double)v.x, (double)v.x, acc);
+            acc = fma((double)v.y, (double)v.y, acc);
+        }
+    }
+    double dummy = 0.0;
+    block_sum2(acc, dummy);
+    if (threadIdx.x == 0) part[blockIdx.x] = acc;
+}
+
+// Sum `count` pairs (re, im) laid out as part[i], part[stride + i]; writes out[0], out[1].
+__global__ void __launch_bounds__(kRedThreads) finish_kernel(const double *__restrict__ part, int count,
+                                                             int stride, double *__restrict__ out)
+{
+    double a = 0.0, b = 0.0;
+    for (int i = threadIdx.x; i < count; i += blockDim.x) {
+        a += part[i];
+        if (stride) b += part[stride + i];
+    }
+    block_sum2(a, b);
+    if (threadIdx.x == 0) {
+        out[0] = a;
+        out[1] = b;
+    }
+}
+
+struct TermGroup {
+    uint64_t xm;
+    int nterms;
+    uint64_t zm[kMaxTermsPerGroup];
+    double cre[kMaxTermsPerGroup];  // coeff * Re(i^{#Y})
+    double cim[kMaxTermsPerGroup];  // coeff * Im(i^{#Y})
+};
+
+// sum_x conj(a[x^xm]) a[x] sum_j c_j i^{ny_j} (-1)^{popc(x & zm_j)}
+template <typename R>
+__global__ void __launch_bounds__(kRedThreads) expect_kernel(const typename Cx<R>::T *__restrict__ a,
+                                                             uint64_t N, const TermGroup *__restrict__ grp,
+                                                             double *__restrict__ part)
+{
+    __shared__ uint64_t zm[kMaxTermsPerGroup];
+    __shared__ R cre[kMaxTermsPerGroup], cim[kMaxTermsPerGroup];
+    const int nt = grp->nterms;
+    const uint64_t xm = grp->xm;
+    for (int j = threadIdx.x; j < nt; j += blockDim.x) {
+        zm[j] = grp->zm[j];
+        cre[j] = (R)grp->cre[j];
+        cim[j] = (R)grp->cim[j];
+    }
+    __syncthreads();
+    const uint64_t per = (N + gridDim.x - 1) / gridDim.x;
+    const uint64_t lo = per * blockIdx.x;
+    const uint64_t hi = lo + per < N ? lo + per : N;
+    double accr = 0.0, acci = 0.0;
+    R fr = 0, fi = 0;
+    int cnt = 0;
+    for (uint64_t x = lo + threadIdx.x; x < hi; x += blockDim.x) {
+        const auto ax = a[x];
+        const auto ay = a[x ^ xm];
+        // v = conj(ay) * ax
+        const R vr = (R)ay.x * (R)ax.x + (R)ay.y * (R)ax.y;
+        const R vi = (R)ay.x * (R)ax.y - (R)ay.y * (R)ax.x;
+        R er = 0, ei = 0;
+        for (int j = 0; j < nt; ++j) {
+            const R s = (__popcll(x & zm[j]) & 1) ? R(-1) : R(1);
+            er = fma(s, cre[j], er);
+            ei = fma(s, cim[j], ei);
+        }
+        // (er + i ei) * (vr + i vi)
+        fr += er * vr - ei * vi;
+        fi += er * vi + ei * vr;
+        if (sizeof(R) == 4 && ++cnt == 32) {
+            accr += (double)fr;
+            acci += (double)fi;
+            fr = fi = 0;
+            cnt = 0;
+        }
+    }
+    accr += (double)fr;
+    acci += (double)fi;
+    block_sum2(accr, acci);
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = accr;
+        part[gridDim.x + blockIdx.x] = acci;
+    }
+}
+
+// Marginal probabilities: hist[m] += |a_x|^2 with m gathered from the bits pos[0..nq).
+template <typename R>
+__global__ void __launch_bounds__(kRedThreads) probs_kernel(const typename Cx<R>::T *__restrict__ a,
+                                                            uint64_t N, int nq, uint4 pos_packed0,
+                                                            uint4 pos_packed1,
+                                                            double *__restrict__ hist)
+{
+    extern __shared__ double sh[];
+    const int M = 1 << nq;
+    const bool use_smem = nq <= 11;
+    if (use_smem)
+        for (int m = threadIdx.x; m < M; m += blockDim.x) sh[m] = 0.0;
+    __syncthreads();
+    uint8_t pos[32];
+    const uint32_t w[8] = {pos_packed0.x, pos_packed0.y, pos_packed0.z, pos_packed0.w,
+                           pos_packed1.x, pos_packed1.y, pos_packed1.z, pos_packed1.w};
+#pragma unroll
+    for (int j = 0; j < 32; ++j) pos[j] = (w[j >> 2] >> (8 * (j & 3))) & 0xff;
+    const uint64_t per = (N + gridDim.x - 1) / gridDim.x;
+    const uint64_t lo = per * blockIdx.x;
+    const uint64_t hi = lo + per < N ? lo + per : N;
+    for (uint64_t x = lo + threadIdx.x; x < hi; x += blockDim.x) {
+        const auto v = a[x];
+        const double p = (double)v.x * (double)v.x + (double)v.y * (double)v.y;
+        uint32_t m = 0;
+        for (int j = 0; j < nq; ++j) m |= uint32_t((x >> pos[j]) & 1) << j;
+        if (use_smem) atomicAdd(&sh[m], p);
+        else atomicAdd(&hist[m], p);
+    }
+    if (use_smem) {
+        __syncthreads();
+        for (int m = threadIdx.x; m < M; m += blockDim.x)
+            if (sh[m] != 0.0) atomicAdd(&hist[m], sh[m]);
+    }
+}
+
+int g_sms = 0;
+int reduce_blocks(uint64_t N)
+{
+    if (!g_sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
+        if (g_sms <= 0) g_sms = 1;
+    }
+    uint64_t b = uint64_t(g_sms) * 8;
+    if (b > kRedBlocksMax) b = kRedBlocksMax;
+    const uint64_t need = (N + kRedThreads - 1) / kRedThreads;
+    if (b > need) b = need;
+    return b < 1 ? 1 : (int)b;
+}
+
+int cuda_fail(const char *what, char *err, size_t errlen)
+{
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) return QS_OK;
+    snprintf(err, errlen, "%s: %s", what, cudaGetErrorString(e));
+    return QS_ECUDA;
+}
+
+}  // namespace
+
+size_t reduce_scratch_bytes()
+{
+    // partials (2 x blocks) + 2 results + one term group
+    return sizeof(double) * (2 * kRedBlocksMax + 8) + sizeof(TermGroup) + 256;
+}
+
+int launch_norm2(const LaunchCtx &c, double *d_scratch, double *h_out, char *err, size_t errlen)
+{
+    const uint64_t N = 1ull << c.n;
+    const int blocks = reduce_blocks(N);
+    cudaStream_t st = (cudaStream_t)c.stream;
+    double *part = d_scratch, *res = d_scratch + 2 * kRedBlocksMax;
+    if (c.dt == QS_C64)
+        norm2_kernel<float><<<blocks, kRedThreads, 0, st>>>((const float2 *)c.amp, N, part);
+    else
+        norm2_kernel<double><<<blocks, kRedThreads, 0, st>>>((const double2 *)c.amp, N, part);
+    finish_kernel<<<1, kRedThreads, 0, st>>>(part, blocks, 0, res);
+    int rc = cuda_fail("norm2 launch", err, errlen);
+    if (rc) return rc;
+    double r[2];
+    if (cudaMemcpyAsync(r, res, sizeof(r), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return cuda_fail("norm2 readback", err, errlen);
+    *h_out = r[0];
+    return QS_OK;
+}
+
+int launch_probs(const LaunchCtx &c, const int *phys_q, int nq, double *d_scratch,
+                 size_t scratch_bytes, double *h_out, char *err, size_t errlen)
+{
+    const uint64_t N = 1ull << c.n;
+    const size_t M = size_t(1) << nq;
+    if (M * sizeof(double) > scratch_bytes) {
+        snprintf(err, errlen, "probs: scratch too small");
+        return QS_EINVAL;
+    }
+    cudaStream_t st = (cudaStream_t)c.stream;
+    uint32_t w[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int j = 0; j < nq; ++j) w[j >> 2] |= uint32_t(phys_q[j] & 0xff) << (8 * (j & 3));
+    uint4 p0 = make_uint4(w[0], w[1], w[2], w[3]), p1 = make_uint4(w[4], w[5], w[6], w[7]);
+    if (cudaMemsetAsync(d_scratch, 0, M * sizeof(double), st) != cudaSuccess)
+        return cuda_fail("probs memset", err, errlen);
+    const int blocks = reduce_blocks(N);
+    const size_t smem = nq <= 11 ? M * sizeof(double) : 0;
+    if (c.dt == QS_C64)
+        probs_kernel<float><<<blocks, kRedThreads, smem, st>>>((const float2 *)c.amp, N, nq, p0, p1,
+                                                               d_scratch);
+    else
+        probs_kernel<double><<<blocks, kRedThreads, smem, st>>>((const double2 *)c.amp, N, nq, p0,
+                                                                p1, d_scratch);
+    int rc = cuda_fail("probs launch", err, errlen);
+    if (rc) return rc;
+    if (cudaMemcpyAsync(h_out, d_scratch, M * sizeof(double), cudaMemcpyDeviceToHost, st) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return cuda_fail("probs readback", err, errlen);
+    return QS_OK;
+}
+
+int launch_expect(const LaunchCtx &c, const uint64_t *xm, const uint64_t *zm, const double *coeff,
+                  size_t nterms, double *d_scratch, size_t scratch_bytes, double *h_out, char *err,
+                  size_t errlen)
+{
+    (void)scratch_bytes;
+    const uint64_t N = 1ull << c.n;
+    cudaStream_t st = (cudaStream_t)c.stream;
+    double *part = d_scratch, *res = d_scratch + 2 * kRedBlocksMax;
+    TermGroup *dgrp = reinterpret_cast<TermGroup *>(d_scratch + 2 * kRedBlocksMax + 8);
+    const int blocks = reduce_blocks(N);
+    std::vector<TermGroup> hgv(1);  // host staging; each copy completes before reuse
+    TermGroup &hg = hgv[0];
+    double tot_r = 0.0, tot_i = 0.0;
+    std::vector<char> done(nterms, 0);
+    for (size_t i = 0; i < nterms; ++i) {
+        if (done[i]) continue;
+        // gather all not-yet-done terms with this X mask (up to the group capacity)
+        hg.xm = xm[i];
+        hg.nterms = 0;
+        for (size_t j = i; j < nterms && hg.nterms < kMaxTermsPerGroup; ++j) {
+            if (done[j] || xm[j] != xm[i]) continue;
+            done[j] = 1;
+            const int ny = __builtin_popcountll(xm[j] & zm[j]) & 3;
+            static const double pr[4] = {1, 0, -1, 0}, pi[4] = {0, 1, 0, -1};
+            hg.zm[hg.nterms] = zm[j];
+            hg.cre[hg.nterms] = coeff[j] * pr[ny];
+            hg.cim[hg.nterms] = coeff[j] * pi[ny];
+            hg.nterms++;
+        }
+        if (cudaMemcpyAsync(dgrp, &hg, sizeof(TermGroup), cudaMemcpyHostToDevice, st) != cudaSuccess)
+            return cuda_fail("expect upload", err, errlen);
+        if (c.dt == QS_C64)
+            expect_kernel<float><<<blocks, kRedThreads, 0, st>>>((const float2 *)c.amp, N, dgrp, part);
+        else
+            expect_kernel<double><<<blocks, kRedThreads, 0, st>>>((const double2 *)c.amp, N, dgrp,
+                                                                  part);
+        finish_kernel<<<1, kRedThreads, 0, st>>>(part, blocks, blocks, res);
+        int rc = cuda_fail("expect launch", err, errlen);
+        if (rc) return rc;
+        double r[2];
+        if (cudaMemcpyAsync(r, res, sizeof(r), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            return cuda_fail("expect readback", err, errlen);
+        tot_r += r[0];
+        tot_i += r[1];
+    }
+    h_out[0] = tot_r;
+    h_out[1] = tot_i;
+    return QS_OK;
+}
+
+__global__ void set_one_kernel(void *amp, uint64_t x, int is64)
+{
+    if (is64) reinterpret_cast<float2 *>(amp)[x] = make_float2(1.f, 0.f);
+    else reinterpret_cast<double2 *>(amp)[x] = make_double2(1.0, 0.0);
+}
+
+int launch_set_basis(const LaunchCtx &c, uint64_t x, char *err, size_t errlen)
+{
+    cudaStream_t st = (cudaStream_t)c.stream;
+    const size_t bytes = (size_t(1) << c.n) * (c.dt == QS_C64 ? 8 : 16);
+    if (cudaMemsetAsync(c.amp, 0, bytes, st) != cudaSuccess)
+        return cuda_fail("set_basis memset", err, errlen);
+    set_one_kernel<<<1, 1, 0, st>>>(c.amp, x, c.dt == QS_C64 ? 1 : 0);
+    return cuda_fail("set_basis launch", err, errlen);
+}
+
+}  // namespace qs

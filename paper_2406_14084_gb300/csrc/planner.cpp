@@ -1,0 +1,827 @@
+// planner.cpp -- host planning for the slab-blocked simulator.
+//
+// 1. canonicalize(): API gates -> canonical gates with FP64 matrices (host libm only; the
+//    device never evaluates transcendental functions).
+// 2. Fusion (arXiv 2406.14084, Alg. 2 level 3 and the diagonal fusion of the artifact
+//    appendix): a greedy scan merges later gates into the current one when they commute with
+//    every gate skipped over and the merged gate stays within a width limit.  Diagonal gates
+//    merge into diagonal tables (D<k> gates); dense merges form k-qubit unitaries whose FP64
+//    product is U = G_m ... G_1, accepted when the analytic cost model says the merged op is
+//    cheaper than the parts.
+// 3. Gate-block finding (Eq. 5-7, Alg. 1 findGBs): repeatedly build one slab pass.  Starting
+//    from the always-resident low segment bits, scan the remaining ops in order and take every
+//    op whose predecessors are done and whose non-diagonal qubits fit the slab (adding their
+//    physical positions while there is room); ops that do not fit block their qubits for the
+//    rest of the scan.  Diagonal roles (controls, diagonal gates) never need slab residence:
+//    outside the slab their bits are constant per CTA.  Uncontrolled SWAP gates only relabel
+//    qubits (Sec. II-B) and cost nothing.  In the paper's low-block mode the slab is fixed to
+//    the b lowest physical bits and remap passes (Alg. 4) bring needed qubits into it.
+#include "planner.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <set>
+
+namespace qs {
+
+namespace {
+
+const double kPi = 3.14159265358979323846;
+
+int popcount(uint64_t x) { return __builtin_popcountll(x); }
+
+// ------------------------------------------------------------------ gate matrices
+
+bool named_matrix(const qs_gate &g, std::vector<cd> &m, bool &diag)
+{
+    const double th = g.p[0], ph = g.p[1], la = g.p[2];
+    const double c = std::cos(th / 2), s = std::sin(th / 2);
+    const cd I(0, 1);
+    diag = false;
+    switch (g.kind) {
+    case QS_H: {
+        const double r = 1.0 / std::sqrt(2.0);
+        m = {r, r, r, -r};
+        return true;
+    }
+    case QS_Y: m = {0.0, -I, I, 0.0}; return true;
+    case QS_RX: m = {c, -I * s, -I * s, c}; return true;
+    case QS_RY: m = {c, -s, s, c}; return true;
+    case QS_U3:
+        m = {c, -std::exp(I * la) * s, std::exp(I * ph) * s, std::exp(I * (ph + la)) * c};
+        return true;
+    case QS_Z: diag = true; m = {1.0, -1.0}; return true;
+    case QS_S: diag = true; m = {1.0, I}; return true;
+    case QS_SDG: diag = true; m = {1.0, -I}; return true;
+    case QS_T: diag = true; m = {1.0, std::exp(I * (kPi / 4))}; return true;
+    case QS_TDG: diag = true; m = {1.0, std::exp(-I * (kPi / 4))}; return true;
+    case QS_RZ: diag = true; m = {std::exp(-I * (th / 2)), std::exp(I * (th / 2))}; return true;
+    case QS_P: diag = true; m = {1.0, std::exp(I * th)}; return true;
+    case QS_CZ: diag = true; m = {1.0, 1.0, 1.0, -1.0}; return true;
+    case QS_CP: diag = true; m = {1.0, 1.0, 1.0, std::exp(I * th)}; return true;
+    case QS_RZZ: {
+        diag = true;
+        const cd e0 = std::exp(-I * (th / 2)), e1 = std::exp(I * (th / 2));
+        m = {e0, e1, e1, e0};
+        return true;
+    }
+    default: return false;
+    }
+}
+
+int expected_nt(int kind)
+{
+    switch (kind) {
+    case QS_CZ: case QS_CP: case QS_SWAP: case QS_RZZ: return 2;
+    case QS_UNITARY: case QS_DIAG: return -1;
+    default: return 1;
+    }
+}
+
+char role_of(const CGate &g, int q)
+{
+    // 'N' = non-diagonal action on q; 'D' = diagonal action (controls, diagonal gates)
+    if (g.cls == C_DIAG) return 'D';
+    for (int t : g.tq)
+        if (t == q) return 'N';
+    return 'D';
+}
+
+std::vector<int> all_qubits(const CGate &g)
+{
+    std::vector<int> v = g.tq;
+    v.insert(v.end(), g.cq.begin(), g.cq.end());
+    return v;
+}
+
+// Dense matrix of g on the ordered qubit list Q (local bit j <-> Q[j]); Q must cover g.
+std::vector<cd> embed(const CGate &g, const std::vector<int> &Q)
+{
+    const int kq = (int)Q.size();
+    const size_t D = size_t(1) << kq;
+    std::vector<cd> M(D * D, 0.0);
+    auto pos = [&](int q) {
+        for (int j = 0; j < kq; ++j)
+            if (Q[j] == q) return j;
+        return -1;
+    };
+    uint64_t cmask = 0;
+    for (int c : g.cq) cmask |= 1ull << pos(c);
+    std::vector<int> tp;
+    for (int t : g.tq) tp.push_back(pos(t));
+    const int kt = (int)tp.size();
+    for (size_t col = 0; col < D; ++col) {
+        if ((col & cmask) != cmask) {
+            M[col * D + col] = 1.0;
+            continue;
+        }
+        uint64_t l = 0;
+        for (int j = 0; j < kt; ++j) l |= ((col >> tp[j]) & 1ull) << j;
+        uint64_t clear = col;
+        for (int j = 0; j < kt; ++j) clear &= ~(1ull << tp[j]);
+        switch (g.cls) {
+        case C_DENSE: {
+            const size_t Dt = size_t(1) << kt;
+            for (size_t r = 0; r < Dt; ++r) {
+                uint64_t row = clear;
+                for (int j = 0; j < kt; ++j) row |= ((r >> j) & 1ull) << tp[j];
+                M[row * D + col] = g.m[r * Dt + l];
+            }
+            break;
+        }
+        case C_DIAG: M[col * D + col] = g.m[l]; break;
+        case C_PERMX: M[(col ^ (1ull << tp[0])) * D + col] = 1.0; break;
+        case C_SWAP: {
+            const uint64_t b0 = (col >> tp[0]) & 1, b1 = (col >> tp[1]) & 1;
+            const uint64_t row = (clear) | (b1 << tp[0]) | (b0 << tp[1]);
+            M[row * D + col] = 1.0;
+            break;
+        }
+        }
+    }
+    return M;
+}
+
+// Diagonal entries of a diagonal gate (controls folded in) on the ordered list Q.
+std::vector<cd> embed_diag(const CGate &g, const std::vector<int> &Q)
+{
+    const int kq = (int)Q.size();
+    const size_t D = size_t(1) << kq;
+    std::vector<cd> d(D, 1.0);
+    auto pos = [&](int q) {
+        for (int j = 0; j < kq; ++j)
+            if (Q[j] == q) return j;
+        return -1;
+    };
+    uint64_t cmask = 0;
+    for (int c : g.cq) cmask |= 1ull << pos(c);
+    std::vector<int> tp;
+    for (int t : g.tq) tp.push_back(pos(t));
+    for (size_t x = 0; x < D; ++x) {
+        if ((x & cmask) != cmask) continue;
+        uint64_t l = 0;
+        for (size_t j = 0; j < tp.size(); ++j) l |= ((x >> tp[j]) & 1ull) << j;
+        d[x] = g.m[l];
+    }
+    return d;
+}
+
+std::vector<cd> matmul(const std::vector<cd> &A, const std::vector<cd> &B, size_t D)
+{
+    std::vector<cd> C(D * D, 0.0);
+    for (size_t i = 0; i < D; ++i)
+        for (size_t k = 0; k < D; ++k) {
+            const cd a = A[i * D + k];
+            if (a == cd(0.0)) continue;
+            for (size_t j = 0; j < D; ++j) C[i * D + j] += a * B[k * D + j];
+        }
+    return C;
+}
+
+std::vector<int> union_qubits(const CGate &a, const CGate &b)
+{
+    std::vector<int> u = all_qubits(a);
+    for (int q : all_qubits(b))
+        if (std::find(u.begin(), u.end(), q) == u.end()) u.push_back(q);
+    return u;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ canonicalisation
+
+int canonicalize(const qs_gate *g, size_t ng, int n, std::vector<CGate> &out, std::string &err)
+{
+    out.clear();
+    out.reserve(ng);
+    for (size_t i = 0; i < ng; ++i) {
+        const qs_gate &x = g[i];
+        char buf[160];
+        if (x.kind < 0 || x.kind >= QS_NUM_KINDS) {
+            snprintf(buf, sizeof buf, "gate %zu: unknown kind %d", i, x.kind);
+            err = buf;
+            return QS_EINVAL;
+        }
+        if (x.nt < 1 || x.nt > QS_MAX_TARGETS || x.nc < 0 || x.nc > QS_MAX_CONTROLS) {
+            snprintf(buf, sizeof buf, "gate %zu: bad target/control count", i);
+            err = buf;
+            return QS_EINVAL;
+        }
+        const int ent = expected_nt(x.kind);
+        if (ent > 0 && x.nt != ent) {
+            snprintf(buf, sizeof buf, "gate %zu: kind %d needs %d targets", i, x.kind, ent);
+            err = buf;
+            return QS_EINVAL;
+        }
+        if (x.kind == QS_CX && x.nc < 1) {
+            snprintf(buf, sizeof buf, "gate %zu: CX needs a control", i);
+            err = buf;
+            return QS_EINVAL;
+        }
+        uint64_t seen = 0;
+        bool bad = false;
+        for (int j = 0; j < x.nt + x.nc; ++j) {
+            const int q = j < x.nt ? x.t[j] : x.c[j - x.nt];
+            if (q < 0 || q >= n || (seen >> q & 1)) bad = true;
+            else seen |= 1ull << q;
+        }
+        if (bad) {
+            snprintf(buf, sizeof buf, "gate %zu: qubit out of range or repeated", i);
+            err = buf;
+            return QS_EINVAL;
+        }
+        CGate c;
+        c.tq.assign(x.t, x.t + x.nt);
+        c.cq.assign(x.c, x.c + x.nc);
+        const size_t D = size_t(1) << x.nt;
+        bool diag = false;
+        if (x.kind == QS_X || x.kind == QS_CX) {
+            c.cls = C_PERMX;
+        } else if (x.kind == QS_SWAP) {
+            c.cls = C_SWAP;
+        } else if (x.kind == QS_UNITARY || x.kind == QS_DIAG) {
+            if (!x.m) {
+                snprintf(buf, sizeof buf, "gate %zu: matrix pointer is NULL", i);
+                err = buf;
+                return QS_EINVAL;
+            }
+            if (x.kind == QS_DIAG) {
+                c.cls = C_DIAG;
+                c.m.resize(D);
+                for (size_t e = 0; e < D; ++e) c.m[e] = cd(x.m[2 * e], x.m[2 * e + 1]);
+            } else {
+                std::vector<cd> m(D * D);
+                for (size_t e = 0; e < D * D; ++e) m[e] = cd(x.m[2 * e], x.m[2 * e + 1]);
+                bool isdiag = true;
+                for (size_t r = 0; r < D && isdiag; ++r)
+                    for (size_t col = 0; col < D; ++col)
+                        if (r != col && m[r * D + col] != cd(0.0)) { isdiag = false; break; }
+                if (isdiag) {
+                    c.cls = C_DIAG;
+                    c.m.resize(D);
+                    for (size_t e = 0; e < D; ++e) c.m[e] = m[e * D + e];
+                } else {
+                    c.cls = C_DENSE;
+                    c.m = std::move(m);
+                }
+            }
+        } else {
+            if (!named_matrix(x, c.m, diag)) {
+                err = "internal: no matrix for gate kind";
+                return QS_EINVAL;
+            }
+            c.cls = diag ? C_DIAG : C_DENSE;
+        }
+        for (const cd &v : c.m)
+            if (!std::isfinite(v.real()) || !std::isfinite(v.imag())) {
+                snprintf(buf, sizeof buf, "gate %zu: non-finite matrix entry", i);
+                err = buf;
+                return QS_EINVAL;
+            }
+        out.push_back(std::move(c));
+    }
+    return QS_OK;
+}
+
+// ------------------------------------------------------------------ cost model
+
+double op_cost(const CGate &g, qs_dtype dt)
+{
+    // Units: FP32 FMA per amplitude.  FP64 arithmetic is weighted 64x (GB300 issues FP64 at a
+    // small fraction of the FP32 rate); a shared-memory round trip of one amplitude costs the
+    // bandwidth equivalent of 16 (complex64) or 32 (complex128) FMA slots per SM cycle share.
+    const double w = dt == QS_C64 ? 1.0 : 64.0;
+    const double ovh = dt == QS_C64 ? 16.0 : 32.0;
+    const int k = (int)g.tq.size();
+    double frac = 1.0;
+    if (g.cls != C_DIAG) frac = std::ldexp(1.0, -(int)g.cq.size());
+    switch (g.cls) {
+    case C_DENSE: return frac * (w * 4.0 * std::ldexp(1.0, k) + ovh) + 2.0;
+    case C_DIAG: {
+        double f = 1.0;
+        const int kk = k + (int)g.cq.size();
+        return f * (w * 4.0 + 3.0 * kk + ovh) + 2.0;
+    }
+    case C_PERMX: return frac * ovh + 2.0;
+    case C_SWAP: return frac * ovh * 0.5 + 2.0;
+    }
+    return 0.0;
+}
+
+int default_slab_bits(qs_dtype dt) { return dt == QS_C64 ? 13 : 12; }
+int default_seg_bits(qs_dtype dt) { return dt == QS_C64 ? 4 : 3; }
+
+// ------------------------------------------------------------------ fusion
+
+namespace {
+
+bool hoistable(const CGate &g, const std::map<int, char> &skipped)
+{
+    for (int q : all_qubits(g)) {
+        auto it = skipped.find(q);
+        if (it == skipped.end()) continue;
+        if (it->second == 'N' || role_of(g, q) == 'N') return false;
+    }
+    return true;
+}
+
+void note_skipped(const CGate &g, std::map<int, char> &skipped)
+{
+    for (int q : all_qubits(g)) {
+        const char r = role_of(g, q);
+        auto it = skipped.find(q);
+        if (it == skipped.end()) skipped[q] = r;
+        else if (r == 'N') it->second = 'N';
+    }
+}
+
+// Merge g (applied after cur) into cur if allowed.  Returns true on success.
+bool try_merge(CGate &cur, const CGate &g, int kdiag, int kdense, bool force_dense, qs_dtype dt)
+{
+    std::vector<int> U = union_qubits(cur, g);
+    if (cur.cls == C_DIAG && g.cls == C_DIAG) {
+        if ((int)U.size() > kdiag) return false;
+        std::vector<cd> a = embed_diag(cur, U), b = embed_diag(g, U);
+        for (size_t i = 0; i < a.size(); ++i) a[i] *= b[i];
+        CGate m;
+        m.cls = C_DIAG;
+        m.tq = U;
+        m.m = std::move(a);
+        m.nsrc = cur.nsrc + g.nsrc;
+        cur = std::move(m);
+        return true;
+    }
+    if (kdense < 1 || (int)U.size() > kdense) return false;
+    // dense merge: matrix over U (controls become qubits of the fused gate)
+    CGate m;
+    m.cls = C_DENSE;
+    m.tq = U;
+    const size_t D = size_t(1) << U.size();
+    m.m = matmul(embed(g, U), embed(cur, U), D);
+    m.nsrc = cur.nsrc + g.nsrc;
+    if (!force_dense) {
+        // keep controls as controls where possible: a merged op is only worth it if cheaper
+        if (op_cost(m, dt) > op_cost(cur, dt) + op_cost(g, dt) + 1e-9) return false;
+    }
+    cur = std::move(m);
+    return true;
+}
+
+std::vector<CGate> fuse_pass(const std::vector<CGate> &in, int kdiag, int kdense, bool force_dense,
+                             bool diag_only, qs_dtype dt)
+{
+    const int window = 256;
+    std::vector<CGate> out;
+    std::vector<char> used(in.size(), 0);
+    for (size_t i = 0; i < in.size(); ++i) {
+        if (used[i]) continue;
+        used[i] = 1;
+        CGate cur = in[i];
+        if (diag_only && cur.cls != C_DIAG) {
+            out.push_back(std::move(cur));
+            continue;
+        }
+        std::map<int, char> skipped;
+        for (size_t j = i + 1; j < in.size() && j < i + window; ++j) {
+            if (used[j]) continue;
+            const CGate &g = in[j];
+            bool merged = false;
+            if (hoistable(g, skipped) && !(diag_only && g.cls != C_DIAG))
+                merged = try_merge(cur, g, kdiag, diag_only ? 0 : kdense, force_dense, dt);
+            if (merged) {
+                used[j] = 1;
+                continue;
+            }
+            note_skipped(g, skipped);
+            // stop once every qubit of cur is blocked by a non-diagonal skipped gate
+            bool all_blocked = true;
+            for (int q : all_qubits(cur)) {
+                auto it = skipped.find(q);
+                if (it == skipped.end() || it->second != 'N') { all_blocked = false; break; }
+            }
+            if (all_blocked) break;
+        }
+        out.push_back(std::move(cur));
+    }
+    return out;
+}
+
+// ------------------------------------------------------------------ device-op construction
+
+struct Coefs {
+    std::vector<cd> &pool;
+    uint32_t push(const std::vector<cd> &v)
+    {
+        const uint32_t off = (uint32_t)pool.size();
+        pool.insert(pool.end(), v.begin(), v.end());
+        return off;
+    }
+};
+
+// local_of[p] = slab-local bit of physical position p, or -1 if p is outside the slab.
+// phys[] = physical position of each logical qubit at the op's turn.
+DevOp make_op(const CGate &g, const std::vector<int> &phys, const int *local_of, Coefs &cf)
+{
+    DevOp op;
+    std::memset(&op, 0, sizeof op);
+    std::vector<int> ins;
+    uint64_t cmask = 0, ocmask = 0;
+    for (int c : g.cq) {
+        const int p = phys[c];
+        const int l = local_of[p];
+        if (l >= 0) {
+            cmask |= 1ull << l;
+            ins.push_back(l);
+        } else {
+            ocmask |= 1ull << p;
+        }
+    }
+    switch (g.cls) {
+    case C_DENSE:
+    case C_PERMX:
+    case C_SWAP: {
+        op.type = g.cls == C_DENSE ? OP_DENSE : g.cls == C_PERMX ? OP_PERMX : OP_SWAP;
+        op.k = (uint8_t)g.tq.size();
+        for (size_t j = 0; j < g.tq.size(); ++j) {
+            const int l = local_of[phys[g.tq[j]]];
+            op.t[j] = (uint8_t)l;
+            ins.push_back(l);
+        }
+        if (g.cls == C_DENSE) op.mat = cf.push(g.m);
+        break;
+    }
+    case C_DIAG: {
+        op.type = OP_DIAG;
+        // table bits: local qubits first (in tq order), then outer ones
+        std::vector<int> locq, outq;
+        for (size_t j = 0; j < g.tq.size(); ++j) {
+            if (local_of[phys[g.tq[j]]] >= 0) locq.push_back((int)j);
+            else outq.push_back((int)j);
+        }
+        op.k = (uint8_t)locq.size();
+        op.nout = (uint8_t)outq.size();
+        for (size_t j = 0; j < locq.size(); ++j) op.t[j] = (uint8_t)local_of[phys[g.tq[locq[j]]]];
+        for (size_t j = 0; j < outq.size(); ++j) op.outpos[j] = (uint8_t)phys[g.tq[outq[j]]];
+        const size_t D = g.m.size();
+        std::vector<cd> tab(D);
+        for (size_t o = 0; o < D; ++o) {
+            size_t idx = 0;
+            for (size_t j = 0; j < locq.size(); ++j) idx |= ((o >> locq[j]) & 1) << j;
+            for (size_t j = 0; j < outq.size(); ++j) idx |= ((o >> outq[j]) & 1) << (locq.size() + j);
+            tab[idx] = g.m[o];
+        }
+        op.mat = cf.push(tab);
+        break;
+    }
+    }
+    std::sort(ins.begin(), ins.end());
+    op.nins = (uint8_t)ins.size();
+    for (size_t j = 0; j < ins.size(); ++j) op.ins[j] = (uint8_t)ins[j];
+    op.cmask = cmask;
+    op.ocmask = ocmask;
+    return op;
+}
+
+struct Sched {
+    int gate;
+    std::vector<int> phys;  // logical -> physical snapshot
+};
+
+void emit_pass(Plan &plan, const std::vector<CGate> &gates, std::vector<int> S, int lo, int b, int n,
+               const std::vector<Sched> &sched, StepKind kind)
+{
+    // pad the slab up to b bits with the lowest unused positions
+    std::set<int> inS(S.begin(), S.end());
+    for (int p = 0; (int)inS.size() < b && p < n; ++p) inS.insert(p);
+    DevPass P;
+    std::memset(&P, 0, sizeof P);
+    std::vector<int> hi;
+    for (int p : inS)
+        if (p >= lo) hi.push_back(p);
+    P.b = (int)inS.size();
+    P.lo = lo;
+    P.nhi = (int)hi.size();
+    for (size_t j = 0; j < hi.size(); ++j) P.hipos[j] = (uint8_t)hi[j];
+    for (int j = 0; j < 32; ++j) P.perm[j] = (uint8_t)j;
+    int local_of[64];
+    for (int p = 0; p < 64; ++p) local_of[p] = -1;
+    for (int p = 0; p < lo; ++p) local_of[p] = p;
+    for (size_t j = 0; j < hi.size(); ++j) local_of[hi[j]] = lo + (int)j;
+    Coefs cf{plan.coef};
+    P.op_begin = (int)plan.ops.size();
+    for (const Sched &s : sched) plan.ops.push_back(make_op(gates[s.gate], s.phys, local_of, cf));
+    P.op_end = (int)plan.ops.size();
+    P.has_perm = 0;
+    plan.steps.push_back({kind, (int)plan.passes.size()});
+    plan.passes.push_back(P);
+}
+
+void emit_remap(Plan &plan, int n, int lo, const std::vector<int> &A, const std::vector<int> &B)
+{
+    std::set<int> inS;
+    for (int p = 0; p < lo; ++p) inS.insert(p);
+    for (int p : A) inS.insert(p);
+    for (int p : B) inS.insert(p);
+    (void)n;
+    DevPass P;
+    std::memset(&P, 0, sizeof P);
+    std::vector<int> hi;
+    for (int p : inS)
+        if (p >= lo) hi.push_back(p);
+    P.b = (int)inS.size();
+    P.lo = lo;
+    P.nhi = (int)hi.size();
+    for (size_t j = 0; j < hi.size(); ++j) P.hipos[j] = (uint8_t)hi[j];
+    int local_of[64];
+    for (int p = 0; p < 64; ++p) local_of[p] = -1;
+    for (int p = 0; p < lo; ++p) local_of[p] = p;
+    for (size_t j = 0; j < hi.size(); ++j) local_of[hi[j]] = lo + (int)j;
+    for (int j = 0; j < 32; ++j) P.perm[j] = (uint8_t)j;
+    for (size_t j = 0; j < A.size(); ++j) {
+        const int la = local_of[A[j]], lb = local_of[B[j]];
+        P.perm[la] = (uint8_t)lb;
+        P.perm[lb] = (uint8_t)la;
+    }
+    P.op_begin = P.op_end = (int)plan.ops.size();
+    P.has_perm = 1;
+    plan.steps.push_back({S_REMAP, (int)plan.passes.size()});
+    plan.passes.push_back(P);
+}
+
+int max_remap_pairs(int bmax, int lo) { return std::max(1, (bmax - lo) / 2); }
+
+}  // namespace
+
+// ------------------------------------------------------------------ remap plans
+
+int plan_remap(int n, qs_dtype dt, const std::vector<int> &A, const std::vector<int> &B, Plan &plan,
+               std::string &err)
+{
+    const int lo = std::min(default_seg_bits(dt), n);
+    const int bmax = std::min(max_slab_bits(dt), n);
+    if (A.size() != B.size()) {
+        err = "remap: A and B differ in length";
+        return QS_EINVAL;
+    }
+    uint64_t used = 0;
+    for (size_t j = 0; j < A.size(); ++j) {
+        for (int p : {A[j], B[j]}) {
+            if (p < 0 || p >= n || (used >> p & 1)) {
+                err = "remap: positions must be distinct and in range";
+                return QS_EINVAL;
+            }
+            used |= 1ull << p;
+        }
+    }
+    // split into passes whose slab (low segment + pair positions) fits on chip
+    std::vector<int> a, b;
+    int extra = 0;
+    for (size_t j = 0; j < A.size(); ++j) {
+        const int add = (A[j] >= lo) + (B[j] >= lo);
+        if (extra + add > bmax - lo && !a.empty()) {
+            emit_remap(plan, n, lo, a, b);
+            a.clear();
+            b.clear();
+            extra = 0;
+        }
+        a.push_back(A[j]);
+        b.push_back(B[j]);
+        extra += add;
+    }
+    if (!a.empty()) emit_remap(plan, n, lo, a, b);
+    return QS_OK;
+}
+
+void plan_canonicalize(int n, qs_dtype dt, const std::vector<int> &phys_of, Plan &plan)
+{
+    const int lo = std::min(default_seg_bits(dt), n);
+    const int bmax = std::min(max_slab_bits(dt), n);
+    std::vector<int> log_of(n);
+    for (int q = 0; q < n; ++q) log_of[phys_of[q]] = q;
+    for (int guard = 0; guard < 4 * n + 8; ++guard) {
+        bool done = true;
+        for (int p = 0; p < n; ++p)
+            if (log_of[p] != p) done = false;
+        if (done) break;
+        std::vector<int> A, B;
+        uint64_t used = 0;
+        int extra = 0;
+        for (int p = 0; p < n; ++p) {
+            if (log_of[p] == p) continue;
+            const int t = log_of[p];  // position p holds logical t, whose home is position t
+            if ((used >> p & 1) || (used >> t & 1)) continue;
+            const int add = (p >= lo) + (t >= lo);
+            if (extra + add > bmax - lo) continue;
+            used |= (1ull << p) | (1ull << t);
+            extra += add;
+            A.push_back(p);
+            B.push_back(t);
+        }
+        emit_remap(plan, n, lo, A, B);
+        for (size_t j = 0; j < A.size(); ++j) std::swap(log_of[A[j]], log_of[B[j]]);
+    }
+}
+
+// ------------------------------------------------------------------ full plan
+
+int build_plan(const std::vector<CGate> &gates_in, int n, qs_dtype dt, const qs_options &opt,
+               Plan &plan, std::string &err)
+{
+    plan.n = n;
+    plan.opt = opt;
+    plan.input_gates = (int)gates_in.size();
+    const bool lowblock = opt.slab_mode == QS_SLAB_REMAP;
+
+    // ---- slab geometry
+    const int lo = opt.seg_bits > 0 ? std::min(opt.seg_bits, n) : std::min(default_seg_bits(dt), n);
+    int b = opt.slab_bits > 0 ? opt.slab_bits : default_slab_bits(dt);
+    b = std::min(b, std::min(max_slab_bits(dt), n));
+    if (b < lo) b = lo;
+    if (b - lo > 12) b = lo + 12;
+    plan.slab_bits = b;
+    plan.seg_bits = lo;
+    const int bmax = std::min(max_slab_bits(dt), n);
+
+    // ---- uncontrolled SWAP gates only relabel qubits (Sec. II-B): drop them and rename the
+    // qubits of later gates.  True qubit q lives on working qubit sigma[q] afterwards.
+    std::vector<int> sigma(n);
+    for (int q = 0; q < n; ++q) sigma[q] = q;
+    std::vector<CGate> gates;
+    gates.reserve(gates_in.size());
+    for (const CGate &g0 : gates_in) {
+        if (g0.cls == C_SWAP && g0.cq.empty()) {
+            std::swap(sigma[g0.tq[0]], sigma[g0.tq[1]]);
+            continue;
+        }
+        CGate g = g0;
+        for (int &q : g.tq) q = sigma[q];
+        for (int &q : g.cq) q = sigma[q];
+        gates.push_back(std::move(g));
+    }
+    auto finish_layout = [&](const std::vector<int> &phys_w) {
+        plan.final_phys_of.assign(n, 0);
+        for (int q = 0; q < n; ++q) plan.final_phys_of[q] = phys_w[sigma[q]];
+    };
+
+    // ---- fusion (a fused dense gate must still fit one slab pass)
+    if (opt.fuse_width > 0) {
+        const int kdiag = opt.diag_bits > 0 ? std::min(opt.diag_bits, kMaxDiagBits) : 10;
+        int kdense = std::min(opt.fuse_width, kMaxDense);
+        if (opt.blocking) kdense = std::min(kdense, lowblock ? b : std::max(1, b - lo));
+        gates = fuse_pass(gates, kdiag, 0, false, true, dt);
+        gates = fuse_pass(gates, kdiag, kdense, false, false, dt);
+    }
+    for (const CGate &g : gates) {
+        if (g.cls == C_DENSE && (int)g.tq.size() > kMaxDense) {
+            err = "dense gates wider than 5 qubits need the tensor-core path";
+            return QS_EUNSUPPORTED;
+        }
+        if (g.cls == C_DIAG && (int)g.tq.size() > kMaxDiagBits) {
+            err = "diagonal gate wider than 12 qubits";
+            return QS_EUNSUPPORTED;
+        }
+    }
+    plan.fused_ops = (int)gates.size();
+    double fl = 0;
+    for (const CGate &g : gates) {
+        const int k = (int)g.tq.size();
+        if (g.cls == C_DENSE) fl += 8.0 * std::ldexp(1.0, k) * std::ldexp(1.0, -(int)g.cq.size());
+        else if (g.cls == C_DIAG) fl += 6.0;
+    }
+    plan.flops_per_amp = fl;
+
+    std::vector<int> phys(n), logi(n);
+    for (int q = 0; q < n; ++q) phys[q] = logi[q] = q;
+    auto is_relabel = [](const CGate &g) { return g.cls == C_SWAP && g.cq.empty(); };
+    int ident_local[64];
+    for (int p = 0; p < 64; ++p) ident_local[p] = p < n ? p : -1;
+    auto emit_unblocked = [&](const CGate &g) {
+        Coefs cf{plan.coef};
+        DevOp op = make_op(g, phys, ident_local, cf);
+        plan.steps.push_back({S_UNBLOCKED, (int)plan.ops.size()});
+        plan.ops.push_back(op);
+    };
+
+    if (!opt.blocking) {
+        // gate-by-gate: one full-state pass per op
+        for (const CGate &g : gates) {
+            if (is_relabel(g)) {
+                std::swap(phys[g.tq[0]], phys[g.tq[1]]);
+                continue;
+            }
+            emit_unblocked(g);
+        }
+        finish_layout(phys);
+        return QS_OK;
+    }
+
+    std::vector<char> done(gates.size(), 0);
+    size_t first = 0;
+    int stalls = 0;
+    while (true) {
+        while (first < gates.size() && done[first]) ++first;
+        if (first >= gates.size()) break;
+        std::set<int> S;
+        for (int p = 0; p < (lowblock ? b : lo); ++p) S.insert(p);
+        std::map<int, char> skipped;
+        std::vector<Sched> sched;
+        std::vector<int> wanted;  // low-block mode: logical qubits needed but not resident
+        for (size_t i = first; i < gates.size(); ++i) {
+            if (done[i]) continue;
+            const CGate &g = gates[i];
+            if (!hoistable(g, skipped)) {
+                note_skipped(g, skipped);
+                continue;
+            }
+            if (is_relabel(g)) {
+                const int a = g.tq[0], c = g.tq[1];
+                std::swap(phys[a], phys[c]);
+                logi[phys[a]] = a;
+                logi[phys[c]] = c;
+                done[i] = 1;
+                continue;
+            }
+            std::vector<int> need;
+            if (g.cls != C_DIAG)
+                for (int t : g.tq)
+                    if (!S.count(phys[t])) need.push_back(phys[t]);
+            const bool fits = lowblock ? need.empty() : (int)(S.size() + need.size()) <= b;
+            if (fits) {
+                for (int p : need) S.insert(p);
+                sched.push_back({(int)i, phys});
+                done[i] = 1;
+            } else {
+                if (lowblock)
+                    for (int p : need)
+                        if (std::find(wanted.begin(), wanted.end(), logi[p]) == wanted.end())
+                            wanted.push_back(logi[p]);
+                note_skipped(g, skipped);
+            }
+        }
+        if (!sched.empty()) {
+            emit_pass(plan, gates, std::vector<int>(S.begin(), S.end()), lo, b, n, sched, S_PASS);
+            stalls = 0;
+        }
+        while (first < gates.size() && done[first]) ++first;
+        if (first >= gates.size()) break;
+        const int mmax = std::min(max_remap_pairs(bmax, lo), b);
+        const CGate &head = gates[first];
+        const bool head_fits_alone =
+            head.cls == C_DIAG || (lowblock ? (int)head.tq.size() <= mmax : (int)head.tq.size() <= b - lo);
+        if (sched.empty() && (!head_fits_alone || stalls > 2)) {
+            // the first remaining op cannot be brought into any slab: apply it unblocked
+            emit_unblocked(head);
+            done[first] = 1;
+            stalls = 0;
+            continue;
+        }
+        if (lowblock && !wanted.empty()) {
+            // Alg. 4: swap wanted qubits into the low block, evicting block qubits (any position
+            // below b) whose next non-diagonal use is farthest away.
+            std::vector<int> nextuse(n, 1 << 30);
+            int pos = 0;
+            for (size_t i = first; i < gates.size(); ++i, ++pos) {
+                if (done[i] || gates[i].cls == C_DIAG) continue;
+                for (int t : gates[i].tq) nextuse[t] = std::min(nextuse[t], pos);
+            }
+            // keep the head op's own qubits first in the wanted list
+            std::vector<int> want;
+            if (head.cls != C_DIAG)
+                for (int t : head.tq)
+                    if (phys[t] >= b) want.push_back(t);
+            for (int q : wanted)
+                if (std::find(want.begin(), want.end(), q) == want.end()) want.push_back(q);
+            std::vector<int> cand;
+            for (int p = 0; p < b; ++p) {
+                const int q = logi[p];
+                bool head_q = false;
+                if (head.cls != C_DIAG)
+                    for (int t : head.tq) head_q |= (t == q);
+                if (!head_q && std::find(want.begin(), want.end(), q) == want.end()) cand.push_back(p);
+            }
+            std::stable_sort(cand.begin(), cand.end(),
+                             [&](int x, int y) { return nextuse[logi[x]] > nextuse[logi[y]]; });
+            std::vector<int> A, B;
+            for (size_t j = 0; j < want.size() && (int)A.size() < mmax && j < cand.size(); ++j) {
+                A.push_back(cand[j]);
+                B.push_back(phys[want[j]]);
+            }
+            if (!A.empty()) {
+                emit_remap(plan, n, lo, A, B);
+                for (size_t j = 0; j < A.size(); ++j) {
+                    const int qa = logi[A[j]], qb = logi[B[j]];
+                    std::swap(phys[qa], phys[qb]);
+                    logi[phys[qa]] = qa;
+                    logi[phys[qb]] = qb;
+                }
+            }
+        }
+        if (sched.empty()) ++stalls;
+    }
+    finish_layout(phys);
+    return QS_OK;
+}
+
+}  // namespace qs

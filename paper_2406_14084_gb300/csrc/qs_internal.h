@@ -1,0 +1,89 @@
+// qs_internal.h -- types shared by the host planner (C++) and the device kernels (CUDA).
+//
+// A plan is a list of steps.  Each step is one full pass over the state in HBM:
+//   PASS       a slab pass (gate block, Alg. 3 of arXiv 2406.14084): every CTA loads one
+//              slab of 2^b amplitudes -- the low `lo` physical bits (a contiguous segment) plus
+//              b-lo further physical bit positions -- applies the block's ops in shared memory,
+//              and stores the slab back, optionally relabelling bits inside the slab;
+//   REMAP      a slab pass with no ops whose store permutation exchanges bit positions
+//              (the in-memory swap of Sec. V-B, Alg. 4);
+//   UNBLOCKED  one op applied directly to the whole state in global memory (gate-by-gate);
+//   TC         a wide fused gate applied as a tensor-core GEMM (complex64 only).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include "qs.h"
+
+namespace qs {
+
+enum OpType : uint8_t {
+    OP_DENSE = 0,  // 2^k x 2^k complex matrix on k local target bits
+    OP_DIAG = 1,   // diagonal table over local bits t[0..k) and outer bits outpos[0..nout)
+    OP_PERMX = 2,  // X on one local bit (swap of amplitude pairs), no arithmetic
+    OP_SWAP = 3,   // exchange of two local bits on the amplitudes where controls hold
+    OP_PHASE = 4,  // multiply by one complex scalar where all cmask bits are 1
+};
+
+constexpr int kMaxSlabBits = 15;    // 2^15 complex64 = 256 KiB; the kernel limit is smem
+constexpr int kMaxDense = 5;        // widest dense op on the SIMT path
+constexpr int kMaxDiagBits = 12;    // widest diagonal table (local + outer qubits)
+constexpr int kMaxIns = 24;         // bit positions inserted when enumerating op groups
+
+// One operation.  In a PASS the bit indices are slab-local (0..b-1) except outpos/ocmask,
+// which are physical positions outside the slab.  In an UNBLOCKED step every index is a
+// physical position of the full state.
+struct DevOp {
+    uint8_t type;
+    uint8_t k;        // DENSE: #targets; DIAG: #local table bits; PERMX: 1; SWAP: 2; PHASE: 0
+    uint8_t nins;     // #positions in ins[]
+    uint8_t nout;     // DIAG: #outer table bits
+    uint8_t t[8];     // target bits (table bits for DIAG), t[0] = LSB of the matrix/table index
+    uint8_t ins[kMaxIns];     // ascending positions forced to 0 (targets) or 1 (controls)
+    uint8_t outpos[kMaxDiagBits];  // DIAG: physical positions of table bits k..k+nout-1
+    uint32_t mat;     // offset of the matrix / table / scalar in the plan's coefficient pool
+    uint32_t pad;
+    uint64_t cmask;   // control bits (same index space as t) that must be 1
+    uint64_t ocmask;  // PASS only: physical control bits outside the slab that must be 1
+};
+
+struct DevPass {
+    int32_t b;         // slab bits
+    int32_t lo;        // low contiguous physical bits (segment = 2^lo amplitudes)
+    int32_t nhi;       // b - lo
+    int32_t op_begin;  // ops [op_begin, op_end) of the plan's op array
+    int32_t op_end;
+    int32_t has_perm;  // store with perm[]
+    uint8_t hipos[32]; // physical positions of local bits lo..b-1, ascending
+    uint8_t perm[32];  // local bit j of the loaded slab is stored at local bit perm[j]
+};
+
+// Launch entry points implemented in the .cu files (host side, stream-ordered).
+// `coef` points to the plan's coefficient pool already converted to the state precision.
+struct LaunchCtx {
+    void *amp;
+    int n;
+    qs_dtype dt;
+    void *stream;  // cudaStream_t
+};
+
+int launch_pass(const LaunchCtx &c, const DevPass *d_pass, const DevPass &h_pass,
+                const DevOp *d_ops, const void *d_coef, int threads, int ctas_per_sm,
+                char *err, size_t errlen);
+int launch_unblocked(const LaunchCtx &c, const DevOp *d_op, const DevOp &h_op,
+                     const void *d_coef, char *err, size_t errlen);
+size_t pass_smem_bytes(qs_dtype dt, int b, int lo);
+int max_slab_bits(qs_dtype dt);
+
+// Reductions (k_reduce.cu).  Scratch is a device buffer of at least reduce_scratch_bytes().
+size_t reduce_scratch_bytes();
+int launch_norm2(const LaunchCtx &c, double *d_scratch, double *h_out, char *err, size_t errlen);
+int launch_probs(const LaunchCtx &c, const int *phys_q, int nq, double *d_scratch,
+                 size_t scratch_bytes, double *h_out, char *err, size_t errlen);
+int launch_expect(const LaunchCtx &c, const uint64_t *xm, const uint64_t *zm,
+                  const double *coeff, size_t nterms, double *d_scratch, size_t scratch_bytes,
+                  double *h_out, char *err, size_t errlen);
+int launch_set_basis(const LaunchCtx &c, uint64_t x, char *err, size_t errlen);
+
+}  // namespace qs

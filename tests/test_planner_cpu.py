@@ -1,0 +1,207 @@
+"""Host-side tests of the C-ABI library that need no GPU: symbol exports, argument validation,
+and the planner, whose listings (qs_plan_dump) are replayed on the FP64 oracle and compared
+with the unfused circuit (fusion products, diagonal tables, slab residency, remaps, relabels).
+"""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2406_14084_gb300 import qs
+from paper_2406_14084_gb300 import workloads as W
+from paper_2406_14084_gb300.workloads import Gate
+
+from plan_replay import replay, to_logical
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+GOLD = os.path.join(ROOT, "tests", "golden")
+
+
+def header_functions():
+    text = open(os.path.join(ROOT, "include", "qs.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(qs_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_library_exports_every_declared_symbol():
+    L = qs.lib()
+    names = header_functions()
+    assert len(names) >= 20
+    for name in names:
+        assert hasattr(L, name), name
+    # the binding mirrors every declared entry point
+    assert set(names) <= set(qs.exported_symbols())
+
+
+def test_version_and_defaults():
+    assert "sm_103a" in qs.qs_version()
+    o = qs.options()
+    assert o.blocking == 1 and o.fuse_width >= 1
+
+
+def rand_state(n, seed):
+    rng = np.random.default_rng(seed)
+    v = rng.normal(size=1 << n) + 1j * rng.normal(size=1 << n)
+    return v / np.linalg.norm(v)
+
+
+ALL = ["H", "X", "Y", "Z", "S", "SDG", "T", "TDG", "RX", "RY", "RZ", "P", "U3", "CX", "CZ",
+       "CP", "SWAP", "RZZ"]
+
+
+def mixed_circuit(n, ng, seed, with_matrices=True, with_controls=True):
+    rng = W.SplitMix64(seed)
+    gates = list(W.random_circuit(n, ng, seed, ALL))
+    if with_controls:
+        out = []
+        for g in gates:
+            free = [q for q in range(n) if q not in g.targets + g.controls]
+            if free and rng.below(4) == 0 and g.kind != "SWAP":
+                out.append(g._replace(controls=g.controls + (free[rng.below(len(free))],)))
+            else:
+                out.append(g)
+        gates = out
+    if with_matrices:
+        for i in range(6):
+            k = 1 + rng.below(3)
+            qs_ = tuple(rng.distinct(n, k))
+            gates.insert(rng.below(len(gates)), Gate("UNITARY", qs_, (), (), W.random_unitary(k, seed + i)))
+            k = 1 + rng.below(4)
+            qs_ = tuple(rng.distinct(n, k))
+            gates.insert(rng.below(len(gates)), Gate("DIAG", qs_, (), (), W.random_diag(k, seed + 50 + i)))
+        gates.insert(3, Gate("SWAP", (0, n - 1), (1,)))
+    return gates
+
+
+def check_plan(gates, n, opts, seed=0):
+    plan = qs.qs_fuse(gates, n, opts)
+    try:
+        text = qs.qs_plan_dump(plan)
+        info = qs.qs_plan_info_get(plan)
+    finally:
+        qs.qs_plan_destroy(plan)
+    a0 = rand_state(n, seed)
+    want = oracle.apply_circuit(n, gates, a0.copy())
+    got = a0.copy()
+    layout, stats = replay(text, got)
+    got_log = to_logical(got, n, layout)
+    err = np.max(np.abs(got_log - want))
+    assert err < 1e-12, err
+    return info, stats
+
+
+@pytest.mark.parametrize("fuse", [0, 1, 2, 3, 5])
+@pytest.mark.parametrize("dtype", [qs.QS_C64, qs.QS_C128])
+def test_gather_plans_match_oracle(fuse, dtype):
+    n = 9
+    gates = mixed_circuit(n, 120, 4000 + fuse)
+    info, stats = check_plan(gates, n, qs.options(fuse_width=fuse, slab_bits=6, seg_bits=2, dtype=dtype))
+    assert stats["max_b"] <= 6
+    assert info["input_gates"] == len(gates)
+
+
+@pytest.mark.parametrize("slab", [4, 5, 7])
+def test_lowblock_remap_plans_match_oracle(slab):
+    n = 10
+    gates = mixed_circuit(n, 100, 77 + slab)
+    info, stats = check_plan(gates, n, qs.options(fuse_width=2, slab_bits=slab, seg_bits=2,
+                                                  slab_mode=qs.QS_SLAB_REMAP))
+    assert stats["remaps"] > 0
+
+
+def test_unblocked_plan_is_one_op_per_gate():
+    n = 7
+    gates = [g for g in mixed_circuit(n, 60, 5, with_matrices=False)
+             if not (g.kind == "SWAP" and not g.controls)]
+    info, stats = check_plan(gates, n, qs.options(fuse_width=0, blocking=0))
+    assert stats["unblocked"] == len(gates) and stats["passes"] == 0
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4])
+def test_tiny_states(n):
+    gates = mixed_circuit(n, 30, 9 + n, with_matrices=False, with_controls=n > 2) if n > 1 else \
+        [Gate("H", (0,)), Gate("T", (0,)), Gate("U3", (0,), (), (0.1, 0.2, 0.3)), Gate("X", (0,))]
+    check_plan(gates, n, qs.options())
+
+
+def test_diagonal_gates_need_no_slab_residence():
+    """Diagonal gates on high qubits fuse into tables applied from outside the slab."""
+    n = 12
+    gates = [Gate("H", (q,)) for q in range(4)]
+    gates += [Gate("CP", (q, 11), (), (0.1 * q,)) for q in range(11)]
+    gates += [Gate("RZZ", (10, 11), (), (0.7,)), Gate("T", (9,))]
+    info, stats = check_plan(gates, n, qs.options(slab_bits=6, seg_bits=2))
+    assert stats["passes"] == 1
+
+
+def test_uncontrolled_swaps_are_relabels():
+    n = 8
+    gates = [Gate("H", (0,)), Gate("SWAP", (0, 7)), Gate("RY", (7,), (), (0.3,)), Gate("SWAP", (3, 5))]
+    info, stats = check_plan(gates, n, qs.options(slab_bits=5, seg_bits=2))
+    # the relabel renames RY's qubit onto H's, so both fuse into one 1-qubit op
+    assert stats["ops"] == 1
+    info, stats = check_plan(gates, n, qs.options(slab_bits=5, seg_bits=2, fuse_width=0))
+    assert stats["ops"] == 2
+
+
+def test_qft_and_layered_plans():
+    n = 12
+    g = W.qft(n)
+    info, _ = check_plan(g, n, qs.options(slab_bits=8, seg_bits=3), seed=1)
+    g = W.layered(n, 6, 1002)
+    info, _ = check_plan(g, n, qs.options(slab_bits=8, seg_bits=3, fuse_width=3), seed=2)
+
+
+def read_listing(path):
+    out = []
+    for line in open(path):
+        if line.strip() and not line.startswith("#"):
+            out.append(line.split())
+    return out
+
+
+def test_worked_example_low_block_plan():
+    """Appendix worked example (10 qubits, chunk size 4): the low-block planner with a 4-qubit
+    block and remap passes reproduces the raw circuit, and never needs more remap passes than
+    the paper's listing has swap lines (5 SQS + 1 CSQS)."""
+    raw = []
+    for f in read_listing(os.path.join(GOLD, "worked_example_raw.txt")):
+        qs_ = tuple(int(v) for v in f[1:-1])
+        raw.append(Gate("H", qs_) if f[0] == "H" else Gate("RZZ", qs_, (), (float(f[-1]),)))
+    info, stats = check_plan(raw, 10, qs.options(fuse_width=0, slab_bits=4, seg_bits=1,
+                                                 slab_mode=qs.QS_SLAB_REMAP))
+    assert stats["remaps"] <= 6
+    # gather slabs: RZZ is diagonal and needs no residence; the H gates touch 7 qubits, one of
+    # them in the 1-bit segment, so 3 free slab positions take two passes and no remap
+    info, stats = check_plan(raw, 10, qs.options(fuse_width=0, slab_bits=4, seg_bits=1))
+    assert stats["passes"] == 2 and stats["remaps"] == 0
+
+
+def test_invalid_inputs_rejected_on_host():
+    with pytest.raises(qs.QsError) as e:
+        qs.qs_fuse([Gate("H", (9,))], 5)
+    assert e.value.status == qs.QS_EINVAL
+    with pytest.raises(qs.QsError):
+        qs.qs_fuse([Gate("CX", (1,), (1,))], 5)
+    with pytest.raises(qs.QsError):
+        qs.qs_fuse([Gate("CX", (1,))], 5)
+    with pytest.raises(qs.QsError):
+        qs.qs_fuse([Gate("UNITARY", (0,), (), (), None)], 5)
+    with pytest.raises(qs.QsError):
+        qs.qs_fuse([Gate("H", (0,))], 0)
+    with pytest.raises(qs.QsError):
+        qs.qs_fuse([Gate("RZ", (0,), (), (float("nan"),))], 3)
+    with pytest.raises(qs.QsError) as e:
+        qs.qs_fuse([Gate("UNITARY", tuple(range(6)), (), (), W.random_unitary(6, 1))], 8,
+                   qs.options(fuse_width=0))
+    assert e.value.status == qs.QS_EUNSUPPORTED
+    assert "tensor-core" in qs.qs_last_error()
+
+
+def test_fault_injection_on_host(monkeypatch):
+    monkeypatch.setenv("QS_FAULT", "plan")
+    with pytest.raises(qs.QsError) as e:
+        qs.qs_fuse([Gate("H", (0,))], 3)
+    assert "injected" in str(e.value)
