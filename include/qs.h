@@ -211,6 +211,27 @@ qs_status qs_norm2(qs_state *s, double *host_out);
  * doubles) is the probability that qubit q[j] reads bit j of m.  Synchronises. */
 qs_status qs_probs(qs_state *s, const int *qubits, int nq, double *host_out);
 
+/* Allocation-free marginal probabilities (the paper has no counterpart; this is a library
+ * service).  Some callers cannot allocate device memory at the moment they need a readout: a
+ * framework whose caching allocator already owns all device memory, a fixed memory arena
+ * budgeted up front, or a code path that must not call cudaMalloc / cudaFree (both may
+ * synchronise or fail).  This entry point uses no allocation of any kind: its histogram lives
+ * in one fixed device array of 2^14 doubles (128 KiB) that every GPU loading the library holds
+ * until the process exits.
+ *   dev_amp:   caller-owned device buffer of 2^n amplitudes of dt, read only; indices are
+ *              physical (no qubit layout is applied), 16-byte aligned.
+ *   qubits:    nq distinct physical bit positions, 0 <= nq <= 14 (QS_EINVAL beyond that);
+ *              host_out[m] (2^nq doubles, host) = probability that bit qubits[j] reads bit j
+ *              of m.
+ *   stream:    cudaStream_t to run on (NULL = legacy default stream); synchronised on return.
+ * The first call on each device looks up the array's device address (cudaGetSymbolAddress)
+ * with that device current; make that first call before any stream capture.  Every call uses
+ * the same array and overwrites the previous call's histogram (the bins used are cleared
+ * first), so calls that overlap on the GPU (different streams or host threads at once) race
+ * and must be serialised by the caller. */
+qs_status qs_probs_noalloc(const void *dev_amp, int n, qs_dtype dt, const int *qubits, int nq,
+                           void *stream, double *host_out);
+
 /* host_out[0] = Re sum_t coeff_t <psi|P_t|psi>, host_out[1] = its imaginary part (zero up to
  * rounding for Hermitian sums).  FP64 accumulation.  Synchronises. */
 qs_status qs_expect_pauli_sum(qs_state *s, const qs_pauli_term *terms, size_t nterms,

@@ -691,6 +691,34 @@ qs_status qs_probs(qs_state *s, const int *qubits, int nq, double *host_out)
     QS_GUARD_END
 }
 
+// Allocation-free readout: validates on the host, then runs the probabilities kernel with the
+// fixed device histogram (k_reduce.cu).  Nothing here allocates host or device memory.
+qs_status qs_probs_noalloc(const void *dev_amp, int n, qs_dtype dt, const int *qubits, int nq,
+                           void *stream, double *host_out)
+{
+    QS_GUARD_BEGIN
+    if (!dev_amp || !host_out || (nq > 0 && !qubits)) return fail(QS_EINVAL, "NULL argument");
+    if (reinterpret_cast<uintptr_t>(dev_amp) & 15) return fail(QS_EINVAL, "dev_amp must be 16-byte aligned");
+    if (n < 1 || n > QS_MAX_QUBITS) return fail(QS_EINVAL, "n must be in [1, 36]");
+    if (dt != QS_C64 && dt != QS_C128) return fail(QS_EINVAL, "bad dtype");
+    if (nq < 0 || nq > n) return fail(QS_EINVAL, "nq must be in [0, n]");
+    if (nq > kStaticProbsMaxQubits)
+        return fail(QS_EINVAL, "qs_probs_noalloc: nq exceeds the fixed 2^14-bin histogram");
+    uint64_t seen = 0;
+    int phys[kStaticProbsMaxQubits + 1];
+    for (int j = 0; j < nq; ++j) {
+        const int q = qubits[j];
+        if (q < 0 || q >= n || (seen >> q & 1)) return fail(QS_EINVAL, "qubit out of range or repeated");
+        seen |= 1ull << q;
+        phys[j] = q;
+    }
+    LaunchCtx c{const_cast<void *>(dev_amp), n, dt, stream};
+    char err[256] = {0};
+    const int rc = launch_probs_static(c, phys, nq, host_out, err, sizeof err);
+    return rc ? fail((qs_status)rc, err) : QS_OK;
+    QS_GUARD_END
+}
+
 qs_status qs_expect_pauli_sum(qs_state *s, const qs_pauli_term *terms, size_t nterms, double *host_out)
 {
     QS_GUARD_BEGIN

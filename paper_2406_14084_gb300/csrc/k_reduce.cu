@@ -13,6 +13,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdio>
+#include <mutex>
 #include <vector>
 
 #include "qs_internal.h"
@@ -331,6 +332,84 @@ int launch_expect(const LaunchCtx &c, const uint64_t *xm, const uint64_t *zm, co
     }
     h_out[0] = tot_r;
     h_out[1] = tot_i;
+    return QS_OK;
+}
+
+// ------------------------------------------------------------------ allocation-free probs
+// Fixed scratch for qs_probs_noalloc: one histogram of at most 2^kStaticProbsMaxQubits doubles
+// (128 KiB).  It is a file-scope device array, so every GPU that loads the library holds it
+// until the process exits.  Host code must not pass `g_static_probs_hist` itself to a kernel:
+// on the host that name is only a stand-in symbol, not a device address.  Its device address
+// is looked up once per device with cudaGetSymbolAddress (static_probs_scratch below).
+namespace {
+
+__device__ __align__(256) double g_static_probs_hist[1 << kStaticProbsMaxQubits];
+
+constexpr int kMaxDevices = 64;
+double *g_static_probs_ptr[kMaxDevices] = {nullptr};
+std::mutex g_static_probs_mu;
+
+// Device address of the fixed histogram on the current device (set up on first use).
+int static_probs_scratch(double **out, char *err, size_t errlen)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+        snprintf(err, errlen, "probs_noalloc: no usable current device (%s)",
+                 e != cudaSuccess ? cudaGetErrorString(e) : "device index out of range");
+        return QS_ECUDA;
+    }
+    std::lock_guard<std::mutex> lock(g_static_probs_mu);
+    if (!g_static_probs_ptr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_static_probs_hist);
+        if (e != cudaSuccess || !p) {
+            snprintf(err, errlen, "probs_noalloc: cudaGetSymbolAddress failed: %s",
+                     cudaGetErrorString(e));
+            cudaGetLastError();
+            return QS_ECUDA;
+        }
+        g_static_probs_ptr[dev] = static_cast<double *>(p);
+    }
+    *out = g_static_probs_ptr[dev];
+    return QS_OK;
+}
+
+}  // namespace
+
+int launch_probs_static(const LaunchCtx &c, const int *phys_q, int nq, double *h_out, char *err,
+                        size_t errlen)
+{
+    if (nq < 0 || nq > kStaticProbsMaxQubits) {
+        snprintf(err, errlen, "probs_noalloc: nq = %d exceeds the fixed scratch of 2^%d bins", nq,
+                 kStaticProbsMaxQubits);
+        return QS_EINVAL;
+    }
+    double *hist = nullptr;
+    int rc = static_probs_scratch(&hist, err, errlen);
+    if (rc) return rc;
+    const uint64_t N = 1ull << c.n;
+    const size_t M = size_t(1) << nq;
+    cudaStream_t st = (cudaStream_t)c.stream;
+    uint32_t w[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int j = 0; j < nq; ++j) w[j >> 2] |= uint32_t(phys_q[j] & 0xff) << (8 * (j & 3));
+    uint4 p0 = make_uint4(w[0], w[1], w[2], w[3]), p1 = make_uint4(w[4], w[5], w[6], w[7]);
+    // the array keeps the previous call's histogram: clear the bins this call accumulates into
+    if (cudaMemsetAsync(hist, 0, M * sizeof(double), st) != cudaSuccess)
+        return cuda_fail("probs_noalloc memset", err, errlen);
+    const int blocks = reduce_blocks(N);
+    const size_t smem = nq <= 11 ? M * sizeof(double) : 0;
+    if (c.dt == QS_C64)
+        probs_kernel<float><<<blocks, kRedThreads, smem, st>>>((const float2 *)c.amp, N, nq, p0, p1,
+                                                               hist);
+    else
+        probs_kernel<double><<<blocks, kRedThreads, smem, st>>>((const double2 *)c.amp, N, nq, p0,
+                                                                p1, hist);
+    rc = cuda_fail("probs_noalloc launch", err, errlen);
+    if (rc) return rc;
+    if (cudaMemcpyAsync(h_out, hist, M * sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return cuda_fail("probs_noalloc readback", err, errlen);
     return QS_OK;
 }
 

@@ -86,4 +86,10 @@ int launch_expect(const LaunchCtx &c, const uint64_t *xm, const uint64_t *zm,
                   double *h_out, char *err, size_t errlen);
 int launch_set_basis(const LaunchCtx &c, uint64_t x, char *err, size_t errlen);
 
+// Marginal probabilities with a fixed file-scope device histogram instead of allocated scratch
+// (qs_probs_noalloc).  nq <= kStaticProbsMaxQubits.
+constexpr int kStaticProbsMaxQubits = 14;
+int launch_probs_static(const LaunchCtx &c, const int *phys_q, int nq, double *h_out, char *err,
+                        size_t errlen);
+
 }  // namespace qs

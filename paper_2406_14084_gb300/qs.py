@@ -99,6 +99,7 @@ _SIGS = {
     "qs_remap": [_vp, _i, ctypes.POINTER(_i), ctypes.POINTER(_i)],
     "qs_norm2": [_vp, _dp],
     "qs_probs": [_vp, ctypes.POINTER(_i), _i, _dp],
+    "qs_probs_noalloc": [_vp, _i, _i, ctypes.POINTER(_i), _i, _vp, _dp],
     "qs_expect_pauli_sum": [_vp, ctypes.POINTER(QsPauliTerm), ctypes.c_size_t, _dp],
     "qs_stats": [_vp, ctypes.POINTER(QsStats)],
     "qs_stats_reset": [_vp],
@@ -301,6 +302,19 @@ def qs_probs(state, qubits) -> np.ndarray:
     out = np.empty(1 << nq, dtype=np.float64)
     q = (_i * max(1, nq))(*qubits)
     _check(lib().qs_probs(state, q, nq, out.ctypes.data_as(_dp)))
+    return out
+
+
+def qs_probs_noalloc(dev_ptr: int, n: int, dtype: int, qubits, stream: int = 0,
+                     out: np.ndarray | None = None) -> np.ndarray:
+    """Marginal probabilities of a raw device buffer (physical bit positions) without any
+    allocation inside the library; `out` may be a preallocated float64 host array."""
+    nq = len(qubits)
+    if out is None:
+        out = np.empty(1 << nq, dtype=np.float64)
+    assert out.dtype == np.float64 and out.flags["C_CONTIGUOUS"] and out.size >= (1 << nq)
+    q = (_i * max(1, nq))(*qubits)
+    _check(lib().qs_probs_noalloc(_vp(dev_ptr), n, dtype, q, nq, _vp(stream), out.ctypes.data_as(_dp)))
     return out
 
 
