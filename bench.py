@@ -178,6 +178,10 @@ def run_gpu(args, w, ws, rank, local):
         opts.slab_bits = args.slab_bits
     if args.slab_mode == "remap":
         opts.slab_mode = qs.QS_SLAB_REMAP
+    if args.stage_bits:
+        opts.stage_bits = args.stage_bits
+    if args.seg_bits:
+        opts.seg_bits = args.seg_bits
     if w["kind"] == "random":
         opts.fuse_width, opts.blocking = 0, 0
 
@@ -295,6 +299,8 @@ def main():
     ap.add_argument("--fuse", type=int, default=None)
     ap.add_argument("--slab-bits", type=int, default=0)
     ap.add_argument("--slab-mode", default="gather", choices=["gather", "remap"])
+    ap.add_argument("--stage-bits", type=int, default=0)
+    ap.add_argument("--seg-bits", type=int, default=0)
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)

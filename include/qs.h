@@ -99,7 +99,9 @@ typedef struct {
     int32_t diag_bits;   /* widest fused diagonal table (qubits), 0 = automatic */
     int32_t dtype;       /* qs_dtype the plan's cost model targets (qs_apply_circuit sets it
                             from the state) */
-    int32_t reserved[5];
+    int32_t stage_bits;  /* register-stage width: slab bits held in registers per thread
+                            (complex64: 4 or 5, complex128: 3 or 4; 0 = automatic) */
+    int32_t reserved[4];
 } qs_options;
 
 /* Plan summary (qs_plan_info). */
@@ -115,6 +117,10 @@ typedef struct {
     double flops_per_amp;  /* modelled arithmetic per amplitude, summed over the plan */
     int64_t device_bytes;  /* bytes the plan uploads to the device (descriptors + coefficients)
                               for a complex128 state; half the coefficient bytes for complex64 */
+    int32_t stages;        /* register stages over all passes */
+    int32_t stage_ops;     /* ops executed inside register stages */
+    int32_t smem_ops;      /* ops executed directly on the shared-memory slab */
+    int32_t stage_bits;    /* register-stage width */
 } qs_plan_info;
 
 /* Per-state counters, accumulated since creation or the last qs_stats_reset.  The *_ms fields

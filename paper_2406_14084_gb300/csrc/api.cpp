@@ -50,6 +50,8 @@ struct DevPlanBuf {
     void *base = nullptr;
     DevPass *passes = nullptr;
     DevOp *ops = nullptr;
+    DevStage *stages = nullptr;
+    DevSub *subs = nullptr;
     void *coef = nullptr;
     int device = -1;
 };
@@ -165,12 +167,17 @@ qs_status upload(qs_plan *pl, qs_dtype dt)
     const Plan &p = pl->p;
     const size_t np = std::max<size_t>(1, p.passes.size()), no = std::max<size_t>(1, p.ops.size());
     const size_t nc = std::max<size_t>(1, p.coef.size());
+    const size_t nst = std::max<size_t>(1, p.stages.size()), nsb = std::max<size_t>(1, p.subs.size());
     auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
-    const size_t o_pass = 0, o_ops = al(np * sizeof(DevPass)), o_coef = o_ops + al(no * sizeof(DevOp));
+    const size_t o_pass = 0, o_ops = al(np * sizeof(DevPass));
+    const size_t o_st = o_ops + al(no * sizeof(DevOp)), o_sb = o_st + al(nst * sizeof(DevStage));
+    const size_t o_coef = o_sb + al(nsb * sizeof(DevSub));
     const size_t total = o_coef + al(nc * amp_bytes(dt));
     std::vector<unsigned char> h(total, 0);
     if (!p.passes.empty()) std::memcpy(h.data() + o_pass, p.passes.data(), p.passes.size() * sizeof(DevPass));
     if (!p.ops.empty()) std::memcpy(h.data() + o_ops, p.ops.data(), p.ops.size() * sizeof(DevOp));
+    if (!p.stages.empty()) std::memcpy(h.data() + o_st, p.stages.data(), p.stages.size() * sizeof(DevStage));
+    if (!p.subs.empty()) std::memcpy(h.data() + o_sb, p.subs.data(), p.subs.size() * sizeof(DevSub));
     if (dt == QS_C64) {
         float *f = reinterpret_cast<float *>(h.data() + o_coef);
         for (size_t i = 0; i < p.coef.size(); ++i) {
@@ -197,17 +204,21 @@ qs_status upload(qs_plan *pl, qs_dtype dt)
     d.device = dev;
     d.passes = reinterpret_cast<DevPass *>((char *)base + o_pass);
     d.ops = reinterpret_cast<DevOp *>((char *)base + o_ops);
+    d.stages = reinterpret_cast<DevStage *>((char *)base + o_st);
+    d.subs = reinterpret_cast<DevSub *>((char *)base + o_sb);
     d.coef = (char *)base + o_coef;
     return QS_OK;
 }
 
-int ctas_per_sm_for(qs_dtype dt, int b, int lo)
+// Synchronise the state's stream and report a bounded device-side wait that ran out.
+qs_status check_device(qs_state *s)
 {
-    const size_t smem = pass_smem_bytes(dt, b, lo) + 1024;
-    int k = (int)((228 * 1024) / smem);
-    if (k < 1) k = 1;
-    if (k > 8) k = 8;
-    return k;
+    int status = 0;
+    if (read_device_status((void *)s->stream, &status) != QS_OK)
+        return fail(QS_ECUDA, "reading the device status word failed");
+    if (status == QS_ETIMEOUT)
+        return fail(QS_ETIMEOUT, "a device-side wait ran out of its iteration budget; results are not valid");
+    return QS_OK;
 }
 
 qs_status run_plan(qs_state *s, qs_plan *pl)
@@ -231,8 +242,9 @@ qs_status run_plan(qs_state *s, qs_plan *pl)
         case S_PASS:
         case S_REMAP: {
             const DevPass &hp = p.passes[stp.index];
-            rc = launch_pass(c, d.passes + stp.index, hp, d.ops, d.coef, 256,
-                             ctas_per_sm_for(s->dt, hp.b, hp.lo), err, sizeof err);
+            const int rb = p.stage_bits > 0 ? p.stage_bits : (s->dt == QS_C64 ? kStageBitsC64 : kStageBitsC128);
+            const PassArgs pa{d.passes + stp.index, d.ops, d.stages, d.subs, d.coef, rb};
+            rc = launch_pass(c, pa, hp, err, sizeof err);
             if (stp.kind == S_PASS) s->stats.passes++;
             else s->stats.remaps++;
             s->stats.bytes_moved += pass_bytes;
@@ -264,6 +276,7 @@ qs_status canonicalize_state(qs_state *s)
     if (identity_layout(s)) return QS_OK;
     std::unique_ptr<qs_plan> pl(new qs_plan());
     pl->p.n = s->n;
+    pl->p.dt = s->dt;
     plan_canonicalize(s->n, s->dt, s->phys_of, pl->p);
     qs_status st = run_plan(s, pl.get());
     if (st) return st;
@@ -382,7 +395,8 @@ qs_status qs_set_stream(qs_state *s, void *stream)
 qs_status qs_sync(qs_state *s)
 {
     if (!s) return fail(QS_EINVAL, "state is NULL");
-    return cuda_status(cudaStreamSynchronize(s->stream), "synchronize");
+    qs_status st = cuda_status(cudaStreamSynchronize(s->stream), "synchronize");
+    return st ? st : check_device(s);
 }
 
 qs_status qs_set_basis(qs_state *s, uint64_t x)
@@ -429,7 +443,8 @@ qs_status qs_copy_to_host(qs_state *s, uint64_t first, uint64_t count, void *hos
                                      cudaMemcpyDeviceToHost, s->stream),
                      "copy to host");
     if (st) return st;
-    return cuda_status(cudaStreamSynchronize(s->stream), "copy to host");
+    st = cuda_status(cudaStreamSynchronize(s->stream), "copy to host");
+    return st ? st : check_device(s);
     QS_GUARD_END
 }
 
@@ -508,7 +523,17 @@ qs_status qs_plan_info_get(const qs_plan *p, qs_plan_info *out)
     out->seg_bits = p->p.seg_bits;
     out->flops_per_amp = p->p.flops_per_amp;
     out->device_bytes = (int64_t)(p->p.passes.size() * sizeof(DevPass) + p->p.ops.size() * sizeof(DevOp) +
+                                  p->p.stages.size() * sizeof(DevStage) + p->p.subs.size() * sizeof(DevSub) +
                                   p->p.coef.size() * 16);
+    out->stages = (int32_t)p->p.stages.size();
+    out->stage_ops = (int32_t)p->p.subs.size();
+    for (const Step &s : p->p.steps)
+        if (s.kind == S_PASS) {
+            const DevPass &P = p->p.passes[s.index];
+            for (int o = P.op_begin; o < P.op_end; ++o)
+                if (p->p.ops[o].type != OP_STAGE) out->smem_ops++;
+        }
+    out->stage_bits = p->p.stage_bits;
     return QS_OK;
 }
 
@@ -584,7 +609,68 @@ qs_status qs_plan_dump(const qs_plan *pl, char *buf, size_t cap, size_t *needed)
             num(P.lo);
             for (int j = 0; j < P.nhi; ++j) num(P.hipos[j]);
             out += "\n";
-            for (int o = P.op_begin; o < P.op_end; ++o) dump_op(p.ops[o], phys_of_local, false);
+            for (int o = P.op_begin; o < P.op_end; ++o) {
+                if (p.ops[o].type != OP_STAGE) {
+                    dump_op(p.ops[o], phys_of_local, false);
+                    continue;
+                }
+                // a register stage: list its sub-ops as ops in physical positions
+                const DevStage &st = p.stages[p.ops[o].mat];
+                auto reg_phys = [&](int j) { return phys_of_local[st.sbits[j]]; };
+                for (int si = st.sub_begin; si < st.sub_end; ++si) {
+                    const DevSub &sb = p.subs[si];
+                    std::vector<int> ctl;
+                    for (int j = 0; j < st.r; ++j)
+                        if (sb.scm >> j & 1) ctl.push_back(reg_phys(j));
+                    for (int l = 0; l < 32; ++l)
+                        if (sb.lcm >> l & 1) ctl.push_back(phys_of_local[l]);
+                    for (int q = 0; q < 64; ++q)
+                        if (sb.ocm >> q & 1) ctl.push_back(q);
+                    auto head = [&](const char *kind, const std::vector<int> &t, const std::vector<int> &c) {
+                        out += "OP ";
+                        out += kind;
+                        num((long long)t.size());
+                        out += " t";
+                        for (int q : t) num(q);
+                        out += " c";
+                        for (int q : c) num(q);
+                    };
+                    switch (sb.type) {
+                    case SB_G1:
+                    case SB_G1R:
+                    case SB_G2: {
+                        std::vector<int> t{reg_phys(sb.j0)};
+                        if (sb.type == SB_G2) t.push_back(reg_phys(sb.j1));
+                        head("DENSE", t, ctl);
+                        out += " m";
+                        for (size_t e = 0; e < (sb.type == SB_G2 ? 16u : 4u); ++e) cnum(p.coef[sb.mat + e]);
+                        break;
+                    }
+                    case SB_X: head("PERMX", {reg_phys(sb.j0)}, ctl); break;
+                    case SB_SWAP: head("SWAP", {reg_phys(sb.j0), reg_phys(sb.j1)}, ctl); break;
+                    case SB_PHASE: {
+                        // controlled phase: diagonal over every masked qubit, 1 except all-ones
+                        head("DIAG", ctl, {});
+                        out += " m";
+                        const size_t D = size_t(1) << ctl.size();
+                        for (size_t e = 0; e + 1 < D; ++e) cnum(cd(1.0));
+                        cnum(p.coef[sb.mat]);
+                        break;
+                    }
+                    case SB_DIAG: {
+                        std::vector<int> t;
+                        for (int j = 0; j < st.r; ++j) t.push_back(reg_phys(j));
+                        for (int j = 0; j < sb.ndl; ++j)
+                            t.push_back(sb.dl[j] & 0x80 ? (sb.dl[j] & 0x7f) : phys_of_local[sb.dl[j]]);
+                        head("DIAG", t, {});
+                        out += " m";
+                        for (size_t e = 0; e < (size_t(1) << t.size()); ++e) cnum(p.coef[sb.mat + e]);
+                        break;
+                    }
+                    }
+                    out += "\n";
+                }
+            }
         }
     }
     out += "LAYOUT";
@@ -605,6 +691,7 @@ qs_status qs_apply_plan(qs_state *s, const qs_plan *p)
     QS_GUARD_BEGIN
     if (!s || !p) return fail(QS_EINVAL, "NULL argument");
     if (p->p.n != s->n) return fail(QS_EINVAL, "plan and state have different qubit counts");
+    if (p->p.dt != s->dt) return fail(QS_EINVAL, "plan was built for the other precision (options.dtype)");
     const int bmax = max_slab_bits(s->dt);
     for (const DevPass &ps : p->p.passes)
         if (ps.b > bmax) return fail(QS_EINVAL, "plan slab too large for this dtype");
@@ -642,6 +729,7 @@ qs_status qs_remap(qs_state *s, int k, const int *A, const int *B)
     std::vector<int> a(A, A + k), b(B, B + k);
     std::unique_ptr<qs_plan> pl(new qs_plan());
     pl->p.n = s->n;
+    pl->p.dt = s->dt;
     std::string err;
     int rc = plan_remap(s->n, s->dt, a, b, pl->p, err);
     if (rc) return fail((qs_status)rc, err);
@@ -665,7 +753,7 @@ qs_status qs_norm2(qs_state *s, double *host_out)
     LaunchCtx c{s->amp, s->n, s->dt, (void *)s->stream};
     char err[256] = {0};
     int rc = launch_norm2(c, s->scratch, host_out, err, sizeof err);
-    return rc ? fail((qs_status)rc, err) : QS_OK;
+    return rc ? fail((qs_status)rc, err) : check_device(s);
     QS_GUARD_END
 }
 

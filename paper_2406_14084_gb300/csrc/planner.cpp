@@ -289,23 +289,35 @@ int canonicalize(const qs_gate *g, size_t ng, int n, std::vector<CGate> &out, st
 
 double op_cost(const CGate &g, qs_dtype dt)
 {
-    // Units: FP32 FMA per amplitude.  FP64 arithmetic is weighted 64x (GB300 issues FP64 at a
-    // small fraction of the FP32 rate); a shared-memory round trip of one amplitude costs the
-    // bandwidth equivalent of 16 (complex64) or 32 (complex128) FMA slots per SM cycle share.
-    const double w = dt == QS_C64 ? 1.0 : 64.0;
-    const double ovh = dt == QS_C64 ? 16.0 : 32.0;
+    // Units: FP32 FMA issue slots per amplitude of the slab kernel.  FP64 arithmetic is
+    // weighted by the measured FP32/FP64 FMA rate ratio of GB300 (~62).  Ops that run inside a
+    // register stage cost their arithmetic plus a small per-op overhead; ops that must run on the
+    // shared-memory slab (dense on 3+ qubits, diagonal tables wider than 7 qubits) also pay a
+    // shared-memory round trip of the whole slab (16 slots for complex64, 32 for complex128).
+    const double w = dt == QS_C64 ? 1.0 : 62.0;
+    const double smem = dt == QS_C64 ? 16.0 : 32.0;
     const int k = (int)g.tq.size();
-    double frac = 1.0;
-    if (g.cls != C_DIAG) frac = std::ldexp(1.0, -(int)g.cq.size());
+    const int nc = (int)g.cq.size();
+    const double frac = std::ldexp(1.0, -nc);
     switch (g.cls) {
-    case C_DENSE: return frac * (w * 4.0 * std::ldexp(1.0, k) + ovh) + 2.0;
+    case C_DENSE:
+        if (k <= 2) return frac * w * 4.0 * std::ldexp(1.0, k) + 1.0;
+        return frac * w * 4.0 * std::ldexp(1.0, k) + smem + 2.0;
     case C_DIAG: {
-        double f = 1.0;
-        const int kk = k + (int)g.cq.size();
-        return f * (w * 4.0 + 3.0 * kk + ovh) + 2.0;
+        bool cphase = true;
+        for (size_t i = 0; i + 1 < g.m.size(); ++i)
+            if (g.m[i] != cd(1.0)) cphase = false;
+        const int m = k + nc;
+        if (cphase) {
+            const cd p = g.m.back();
+            const double flops = (p == cd(-1.0)) ? 0.5 : w * 4.0;  // sign flip vs complex multiply
+            return std::ldexp(1.0, -m) * flops + 1.0;
+        }
+        if (m <= 7) return w * 4.0 + 2.0;
+        return w * 4.0 + 3.0 * m + smem + 2.0;
     }
-    case C_PERMX: return frac * ovh + 2.0;
-    case C_SWAP: return frac * ovh * 0.5 + 2.0;
+    case C_PERMX: return frac * 1.0 + 1.0;
+    case C_SWAP: return frac * 1.0 + 1.0;
     }
     return 0.0;
 }
@@ -350,6 +362,7 @@ bool try_merge(CGate &cur, const CGate &g, int kdiag, int kdense, bool force_den
         m.tq = U;
         m.m = std::move(a);
         m.nsrc = cur.nsrc + g.nsrc;
+        if (!force_dense && op_cost(m, dt) > op_cost(cur, dt) + op_cost(g, dt) + 1e-9) return false;
         cur = std::move(m);
         return true;
     }
@@ -489,8 +502,224 @@ struct Sched {
     std::vector<int> phys;  // logical -> physical snapshot
 };
 
+// The kernel's XOR swizzle of slab-local indices in shared memory (same map as the device's
+// swz<>: complex64 XORs bits 1-3 with bits 5-7 and 9-11, complex128 bits 0-2 with 3-5, 6-8, 9-11).
+uint32_t smem_swizzle(uint32_t i, qs_dtype dt)
+{
+    if (dt == QS_C64) return i ^ (((i >> 4) ^ (i >> 8)) & 0xEu);
+    return i ^ (((i >> 3) ^ (i >> 6) ^ (i >> 9)) & 7u);
+}
+
+// A diagonal gate whose entries are all 1 except the last one (all qubits 1): Z, S, T, P, CZ,
+// CP and their controlled forms.
+bool controlled_phase(const CGate &g, cd &phase)
+{
+    if (g.cls != C_DIAG || g.m.empty()) return false;
+    for (size_t i = 0; i + 1 < g.m.size(); ++i)
+        if (g.m[i] != cd(1.0)) return false;
+    phase = g.m.back();
+    return true;
+}
+
+// Split a pass's scheduled ops into register stages (Alg. 2's innermost fusion level applied
+// to the register file) and shared-memory ops.  A stage collects ops whose non-diagonal local
+// bits fit `RB` register bits; ops are taken in order and may move ahead of skipped ops only if
+// they commute with them (same role test as the block finder).
+void build_stages(Plan &plan, const std::vector<CGate> &gates, const std::vector<Sched> &sched,
+                  const int *local_of, int b, qs_dtype dt, Coefs &cf)
+{
+    (void)dt;
+    const int RB = plan.stage_bits;
+    const size_t ns = sched.size();
+    std::vector<uint64_t> nb(ns, 0), db(ns, 0);
+    std::vector<char> regable(ns, 0), done(ns, 0);
+    for (size_t i = 0; i < ns; ++i) {
+        const CGate &g = gates[sched[i].gate];
+        const std::vector<int> &ph = sched[i].phys;
+        for (int t : g.tq) {
+            const int l = local_of[ph[t]];
+            if (g.cls == C_DIAG) {
+                if (l >= 0) db[i] |= 1ull << l;
+            } else {
+                nb[i] |= 1ull << l;
+            }
+        }
+        for (int c : g.cq) {
+            const int l = local_of[ph[c]];
+            if (l >= 0) db[i] |= 1ull << l;
+        }
+        cd ph0;
+        bool r = b >= RB && b - RB <= 16;
+        if (r) {
+            switch (g.cls) {
+            case C_DENSE: r = g.tq.size() <= 2; break;
+            case C_PERMX: case C_SWAP: r = true; break;
+            case C_DIAG: r = controlled_phase(g, ph0) || (g.tq.size() + g.cq.size() <= 7); break;
+            }
+        }
+        regable[i] = r;
+    }
+    size_t first = 0;
+    while (true) {
+        while (first < ns && done[first]) ++first;
+        if (first >= ns) break;
+        if (!regable[first]) {
+            plan.ops.push_back(make_op(gates[sched[first].gate], sched[first].phys, local_of, cf));
+            done[first] = 1;
+            continue;
+        }
+        uint64_t S = 0, skipN = 0, skipD = 0;
+        std::vector<size_t> sub;
+        for (size_t j = first; j < ns; ++j) {
+            if (done[j]) continue;
+            const bool hoist = (nb[j] & (skipN | skipD)) == 0 && (db[j] & skipN) == 0;
+            if (!hoist || !regable[j]) {
+                skipN |= nb[j];
+                skipD |= db[j];
+                continue;
+            }
+            const uint64_t need = nb[j] & ~S;
+            if (popcount(S | need) <= RB) {
+                S |= need;
+                sub.push_back(j);
+                done[j] = 1;
+            } else {
+                skipN |= nb[j];
+                skipD |= db[j];
+            }
+        }
+        // fill the register set: bits the stage's diagonal ops read first, then high bits
+        uint64_t want = 0;
+        for (size_t j : sub) want |= db[j];
+        for (int l = b - 1; l >= 0 && popcount(S) < RB; --l)
+            if ((want >> l & 1) && !(S >> l & 1)) S |= 1ull << l;
+        for (int l = b - 1; l >= 0 && popcount(S) < RB; --l)
+            if (!(S >> l & 1)) S |= 1ull << l;
+        DevStage st;
+        std::memset(&st, 0, sizeof st);
+        st.r = (uint8_t)RB;
+        int regidx[64];
+        for (int l = 0; l < 64; ++l) regidx[l] = -1;
+        int nr = 0, nrest = 0;
+        for (int l = 0; l < b; ++l) {
+            if (S >> l & 1) {
+                st.sbits[nr] = (uint8_t)l;
+                regidx[l] = nr++;
+            } else {
+                st.rest[nrest++] = (uint8_t)l;
+            }
+        }
+        st.nrest = (uint8_t)nrest;
+        for (int e = 0; e < (1 << RB); ++e) {
+            uint32_t o = 0;
+            for (int j = 0; j < RB; ++j)
+                if (e >> j & 1) o |= 1u << st.sbits[j];
+            st.off[e] = (uint16_t)smem_swizzle(o, plan.dt);
+        }
+        st.sub_begin = (int)plan.subs.size();
+        for (size_t j : sub) {
+            const CGate &g = gates[sched[j].gate];
+            const std::vector<int> &ph = sched[j].phys;
+            DevSub s;
+            std::memset(&s, 0, sizeof s);
+            auto classify = [&](int q) {
+                const int l = local_of[ph[q]];
+                if (l < 0) s.ocm |= 1ull << ph[q];
+                else if (regidx[l] >= 0) s.scm |= 1u << regidx[l];
+                else s.lcm |= 1u << l;
+            };
+            cd phase;
+            if (g.cls != C_DIAG)
+                for (int c : g.cq) classify(c);
+            switch (g.cls) {
+            case C_DENSE:
+                if (g.tq.size() == 1) {
+                    bool real = true;
+                    for (const cd &x : g.m) real = real && x.imag() == 0.0;
+                    s.type = real ? SB_G1R : SB_G1;
+                    s.j0 = (uint8_t)regidx[local_of[ph[g.tq[0]]]];
+                    s.mat = cf.push(g.m);
+                } else {
+                    int j0 = regidx[local_of[ph[g.tq[0]]]], j1 = regidx[local_of[ph[g.tq[1]]]];
+                    std::vector<cd> m = g.m;
+                    if (j0 > j1) {
+                        // exchange the two index bits of rows and columns
+                        auto sw = [](int x) { return ((x & 1) << 1) | ((x >> 1) & 1); };
+                        for (int r = 0; r < 4; ++r)
+                            for (int c = 0; c < 4; ++c) m[sw(r) * 4 + sw(c)] = g.m[r * 4 + c];
+                        std::swap(j0, j1);
+                    }
+                    s.type = SB_G2;
+                    s.j0 = (uint8_t)j0;
+                    s.j1 = (uint8_t)j1;
+                    s.mat = cf.push(m);
+                }
+                break;
+            case C_PERMX:
+                s.type = SB_X;
+                s.j0 = (uint8_t)regidx[local_of[ph[g.tq[0]]]];
+                break;
+            case C_SWAP: {
+                int j0 = regidx[local_of[ph[g.tq[0]]]], j1 = regidx[local_of[ph[g.tq[1]]]];
+                if (j0 > j1) std::swap(j0, j1);
+                s.type = SB_SWAP;
+                s.j0 = (uint8_t)j0;
+                s.j1 = (uint8_t)j1;
+                break;
+            }
+            case C_DIAG:
+                if (controlled_phase(g, phase)) {
+                    s.type = SB_PHASE;
+                    for (int q : g.tq) classify(q);
+                    for (int c : g.cq) classify(c);
+                    s.mat = cf.push(std::vector<cd>{phase});
+                } else {
+                    s.type = SB_DIAG;
+                    std::vector<int> Q = g.tq;
+                    Q.insert(Q.end(), g.cq.begin(), g.cq.end());
+                    const int ntq = (int)g.tq.size();
+                    std::vector<int> qreg(Q.size(), -1), qhi(Q.size(), -1);
+                    int ndl = 0;
+                    for (size_t k = 0; k < Q.size(); ++k) {
+                        const int l = local_of[ph[Q[k]]];
+                        if (l >= 0 && regidx[l] >= 0) {
+                            qreg[k] = regidx[l];
+                        } else {
+                            qhi[k] = ndl;
+                            s.dl[ndl++] = l >= 0 ? (uint8_t)l : (uint8_t)(0x80 | ph[Q[k]]);
+                        }
+                    }
+                    s.ndl = (uint8_t)ndl;
+                    std::vector<cd> tab(size_t(1) << (RB + ndl));
+                    for (size_t hi = 0; hi < (size_t(1) << ndl); ++hi)
+                        for (int e = 0; e < (1 << RB); ++e) {
+                            bool ctl_ok = true;
+                            size_t idx = 0;
+                            for (size_t k = 0; k < Q.size(); ++k) {
+                                const size_t bit = qreg[k] >= 0 ? ((e >> qreg[k]) & 1) : ((hi >> qhi[k]) & 1);
+                                if ((int)k < ntq) idx |= bit << k;
+                                else if (!bit) ctl_ok = false;
+                            }
+                            tab[(hi << RB) | e] = ctl_ok ? g.m[idx] : cd(1.0);
+                        }
+                    s.mat = cf.push(tab);
+                }
+                break;
+            }
+            plan.subs.push_back(s);
+        }
+        st.sub_end = (int)plan.subs.size();
+        DevOp op;
+        std::memset(&op, 0, sizeof op);
+        op.type = OP_STAGE;
+        op.mat = (uint32_t)plan.stages.size();
+        plan.stages.push_back(st);
+        plan.ops.push_back(op);
+    }
+}
+
 void emit_pass(Plan &plan, const std::vector<CGate> &gates, std::vector<int> S, int lo, int b, int n,
-               const std::vector<Sched> &sched, StepKind kind)
+               const std::vector<Sched> &sched, StepKind kind, qs_dtype dt)
 {
     // pad the slab up to b bits with the lowest unused positions
     std::set<int> inS(S.begin(), S.end());
@@ -511,7 +740,7 @@ void emit_pass(Plan &plan, const std::vector<CGate> &gates, std::vector<int> S, 
     for (size_t j = 0; j < hi.size(); ++j) local_of[hi[j]] = lo + (int)j;
     Coefs cf{plan.coef};
     P.op_begin = (int)plan.ops.size();
-    for (const Sched &s : sched) plan.ops.push_back(make_op(gates[s.gate], s.phys, local_of, cf));
+    build_stages(plan, gates, sched, local_of, P.b, dt, cf);
     P.op_end = (int)plan.ops.size();
     P.has_perm = 0;
     plan.steps.push_back({kind, (int)plan.passes.size()});
@@ -630,7 +859,15 @@ int build_plan(const std::vector<CGate> &gates_in, int n, qs_dtype dt, const qs_
                Plan &plan, std::string &err)
 {
     plan.n = n;
+    plan.dt = dt;
     plan.opt = opt;
+    {
+        const int def = dt == QS_C64 ? kStageBitsC64 : kStageBitsC128;
+        int rb = opt.stage_bits > 0 ? opt.stage_bits : def;
+        if (rb > def) rb = def;
+        if (rb < def - 1) rb = def - 1;
+        plan.stage_bits = rb;
+    }
     plan.input_gates = (int)gates_in.size();
     const bool lowblock = opt.slab_mode == QS_SLAB_REMAP;
 
@@ -761,7 +998,7 @@ int build_plan(const std::vector<CGate> &gates_in, int n, qs_dtype dt, const qs_
             }
         }
         if (!sched.empty()) {
-            emit_pass(plan, gates, std::vector<int>(S.begin(), S.end()), lo, b, n, sched, S_PASS);
+            emit_pass(plan, gates, std::vector<int>(S.begin(), S.end()), lo, b, n, sched, S_PASS, dt);
             stalls = 0;
         }
         while (first < gates.size() && done[first]) ++first;

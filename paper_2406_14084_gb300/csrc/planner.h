@@ -39,10 +39,14 @@ struct TcGate {
 
 struct Plan {
     int n = 0;
+    qs_dtype dt = QS_C64;        // precision the plan's register stages are laid out for
+    int stage_bits = 0;          // register-stage width (bits per thread group)
     qs_options opt{};
     std::vector<Step> steps;
     std::vector<DevPass> passes;
     std::vector<DevOp> ops;
+    std::vector<DevStage> stages;
+    std::vector<DevSub> subs;
     std::vector<cd> coef;        // matrices, tables and scalars, FP64
     std::vector<TcGate> tc;
     std::vector<int> final_phys_of;  // logical -> physical after the plan

@@ -59,6 +59,51 @@ struct DevPass {
     uint8_t perm[32];  // local bit j of the loaded slab is stored at local bit perm[j]
 };
 
+// Register stage: ops whose non-diagonal bits all lie in `r` slab-local bits ("register bits")
+// run in registers.  Each thread loads the 2^r amplitudes of one group (all register-bit
+// combinations at fixed values of the other local bits) from shared memory, applies every
+// sub-op of the stage, and stores them back: one shared-memory round trip per stage instead of
+// one per op.  A plan op of type OP_STAGE points at one DevStage (field mat = stage index).
+constexpr int kStageBitsC64 = 5;   // 32 complex64 amplitudes per thread (64 registers)
+constexpr int kStageBitsC128 = 4;  // 16 complex128 amplitudes per thread (64 registers)
+constexpr uint8_t OP_STAGE = 5;
+
+enum SubType : uint8_t {
+    SB_G1 = 0,     // 2x2 matrix on register bit j0
+    SB_G2 = 1,     // 4x4 matrix on register bits j0 < j1 (matrix index bit 0 <-> j0)
+    SB_X = 2,      // X on register bit j0
+    SB_SWAP = 3,   // exchange of register bits j0, j1
+    SB_PHASE = 4,  // multiply by coef[mat] where all masked bits are 1 (controlled phase)
+    SB_DIAG = 5,   // diagonal table expanded over all register bits (see DevSub)
+    SB_G1R = 6,    // 2x2 matrix with real entries on register bit j0
+};
+
+struct DevSub {
+    uint8_t type;
+    uint8_t j0, j1;
+    uint8_t ndl;       // SB_DIAG: non-register table bits
+    uint32_t scm;      // register bits that must be 1 (controls / phase bits)
+    uint32_t lcm;      // slab-local non-register bits that must be 1
+    uint32_t mat;      // coefficient offset (matrix, scalar, or expanded table)
+    uint64_t ocm;      // physical bits outside the slab that must be 1
+    // SB_DIAG: the table holds 2^(r + ndl) entries, index = (hi << r) | e where e is the
+    // register index and bit j of hi comes from slab-local bit dl[j] (dl[j] < 0x80) or from
+    // physical bit (dl[j] & 0x7f) outside the slab (dl[j] >= 0x80).
+    uint8_t dl[12];
+    uint8_t pad[4];
+};
+
+struct DevStage {
+    uint8_t r;          // register bits
+    uint8_t nrest;      // non-register slab-local bits
+    uint8_t sbits[6];   // slab-local position of register bit j
+    uint8_t rest[16];   // non-register slab-local bits; group index bit j -> rest[j]
+    uint16_t off[32];   // slab-local offset of register index e
+    int32_t sub_begin, sub_end;
+};
+
+int num_sms();
+
 // Launch entry points implemented in the .cu files (host side, stream-ordered).
 // `coef` points to the plan's coefficient pool already converted to the state precision.
 struct LaunchCtx {
@@ -68,9 +113,18 @@ struct LaunchCtx {
     void *stream;  // cudaStream_t
 };
 
-int launch_pass(const LaunchCtx &c, const DevPass *d_pass, const DevPass &h_pass,
-                const DevOp *d_ops, const void *d_coef, int threads, int ctas_per_sm,
-                char *err, size_t errlen);
+struct PassArgs {
+    const DevPass *pass;      // device
+    const DevOp *ops;         // device, whole plan
+    const DevStage *stages;   // device, whole plan
+    const DevSub *subs;       // device, whole plan
+    const void *coef;         // device, whole plan, state precision
+    int stage_bits;           // register-stage width the plan was built for
+};
+int launch_pass(const LaunchCtx &c, const PassArgs &a, const DevPass &h_pass, char *err,
+                size_t errlen);
+// Device status word written by bounded waits that ran out (0 = fine).  Reading clears it.
+int read_device_status(void *stream, int *status);
 int launch_unblocked(const LaunchCtx &c, const DevOp *d_op, const DevOp &h_op,
                      const void *d_coef, char *err, size_t errlen);
 size_t pass_smem_bytes(qs_dtype dt, int b, int lo);

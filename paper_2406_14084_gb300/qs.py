@@ -53,7 +53,7 @@ class QsOptions(ctypes.Structure):
                 ("slab_mode", ctypes.c_int32), ("planner", ctypes.c_int32), ("tc", ctypes.c_int32),
                 ("tc_width", ctypes.c_int32), ("graph", ctypes.c_int32),
                 ("diag_bits", ctypes.c_int32), ("dtype", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 5)]
+                ("stage_bits", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
 
 
 class QsPlanInfo(ctypes.Structure):
@@ -61,7 +61,9 @@ class QsPlanInfo(ctypes.Structure):
                 ("unblocked", ctypes.c_int32), ("tc_gates", ctypes.c_int32), ("ops", ctypes.c_int32),
                 ("input_gates", ctypes.c_int32), ("slab_bits", ctypes.c_int32),
                 ("seg_bits", ctypes.c_int32), ("flops_per_amp", ctypes.c_double),
-                ("device_bytes", ctypes.c_int64)]
+                ("device_bytes", ctypes.c_int64), ("stages", ctypes.c_int32),
+                ("stage_ops", ctypes.c_int32), ("smem_ops", ctypes.c_int32),
+                ("stage_bits", ctypes.c_int32)]
 
 
 class QsStats(ctypes.Structure):
