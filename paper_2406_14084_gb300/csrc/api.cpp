@@ -52,6 +52,8 @@ struct DevPlanBuf {
     DevOp *ops = nullptr;
     DevStage *stages = nullptr;
     DevSub *subs = nullptr;
+    DevTc *tcs = nullptr;
+    unsigned char *images = nullptr;
     void *coef = nullptr;
     int device = -1;
 };
@@ -171,13 +173,17 @@ qs_status upload(qs_plan *pl, qs_dtype dt)
     auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
     const size_t o_pass = 0, o_ops = al(np * sizeof(DevPass));
     const size_t o_st = o_ops + al(no * sizeof(DevOp)), o_sb = o_st + al(nst * sizeof(DevStage));
-    const size_t o_coef = o_sb + al(nsb * sizeof(DevSub));
+    const size_t ntc = std::max<size_t>(1, p.tcs.size()), nim = std::max<size_t>(16, p.tc_images.size());
+    const size_t o_tc = o_sb + al(nsb * sizeof(DevSub)), o_im = o_tc + al(ntc * sizeof(DevTc));
+    const size_t o_coef = o_im + al(nim);
     const size_t total = o_coef + al(nc * amp_bytes(dt));
     std::vector<unsigned char> h(total, 0);
     if (!p.passes.empty()) std::memcpy(h.data() + o_pass, p.passes.data(), p.passes.size() * sizeof(DevPass));
     if (!p.ops.empty()) std::memcpy(h.data() + o_ops, p.ops.data(), p.ops.size() * sizeof(DevOp));
     if (!p.stages.empty()) std::memcpy(h.data() + o_st, p.stages.data(), p.stages.size() * sizeof(DevStage));
     if (!p.subs.empty()) std::memcpy(h.data() + o_sb, p.subs.data(), p.subs.size() * sizeof(DevSub));
+    if (!p.tcs.empty()) std::memcpy(h.data() + o_tc, p.tcs.data(), p.tcs.size() * sizeof(DevTc));
+    if (!p.tc_images.empty()) std::memcpy(h.data() + o_im, p.tc_images.data(), p.tc_images.size());
     if (dt == QS_C64) {
         float *f = reinterpret_cast<float *>(h.data() + o_coef);
         for (size_t i = 0; i < p.coef.size(); ++i) {
@@ -206,6 +212,8 @@ qs_status upload(qs_plan *pl, qs_dtype dt)
     d.ops = reinterpret_cast<DevOp *>((char *)base + o_ops);
     d.stages = reinterpret_cast<DevStage *>((char *)base + o_st);
     d.subs = reinterpret_cast<DevSub *>((char *)base + o_sb);
+    d.tcs = reinterpret_cast<DevTc *>((char *)base + o_tc);
+    d.images = reinterpret_cast<unsigned char *>((char *)base + o_im);
     d.coef = (char *)base + o_coef;
     return QS_OK;
 }
@@ -256,7 +264,10 @@ qs_status run_plan(qs_state *s, qs_plan *pl)
             s->stats.bytes_moved += pass_bytes;
             break;
         case S_TC:
-            return fail(QS_EUNSUPPORTED, "tensor-core step in a plan without tensor-core support");
+            rc = launch_tc(c, d.tcs + stp.index, p.tcs[stp.index], d.images, err, sizeof err);
+            s->stats.tc_gates++;
+            s->stats.bytes_moved += pass_bytes;
+            break;
         }
         if (s->profiling) {
             cudaEvent_t ev1 = s->take_event();
@@ -524,6 +535,7 @@ qs_status qs_plan_info_get(const qs_plan *p, qs_plan_info *out)
     out->flops_per_amp = p->p.flops_per_amp;
     out->device_bytes = (int64_t)(p->p.passes.size() * sizeof(DevPass) + p->p.ops.size() * sizeof(DevOp) +
                                   p->p.stages.size() * sizeof(DevStage) + p->p.subs.size() * sizeof(DevSub) +
+                                  p->p.tcs.size() * sizeof(DevTc) + p->p.tc_images.size() +
                                   p->p.coef.size() * 16);
     out->stages = (int32_t)p->p.stages.size();
     out->stage_ops = (int32_t)p->p.subs.size();
@@ -582,7 +594,20 @@ qs_status qs_plan_dump(const qs_plan *pl, char *buf, size_t cap, size_t *needed)
         out += "\n";
     };
     for (const Step &s : p.steps) {
-        if (s.kind == S_UNBLOCKED) {
+        if (s.kind == S_TC) {
+            const DevTc &T = p.tcs[s.index];
+            out += "PASS";
+            num(T.slab.b);
+            num(T.slab.lo);
+            for (int j = 0; j < T.slab.nhi; ++j) num(T.slab.hipos[j]);
+            out += "\nOP DENSE";
+            num(kTcTargets);
+            out += " t";
+            for (int q : p.tc_phys[s.index]) num(q);
+            out += " c m";
+            for (size_t e = 0; e < (size_t(1) << (2 * kTcTargets)); ++e) cnum(p.coef[p.tc_coef[s.index] + e]);
+            out += "\n";
+        } else if (s.kind == S_UNBLOCKED) {
             out += "UNBLOCKED\n";
             dump_op(p.ops[s.index], nullptr, true);
         } else if (s.kind == S_PASS || s.kind == S_REMAP) {

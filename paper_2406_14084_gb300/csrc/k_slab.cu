@@ -601,6 +601,24 @@ int launch_pass(const LaunchCtx &c, const PassArgs &a, const DevPass &h, char *e
     return launch_pass_t<double, kStageBitsC128, 256>(c, a, h, err, errlen);
 }
 
+// Device address of the status word on the current device (for kernels in other files).
+int *device_status_ptr()
+{
+    static int *ptr[64] = {nullptr};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) return nullptr;
+    if (!ptr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_qs_device_status) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        ptr[dev] = static_cast<int *>(p);
+    }
+    return ptr[dev];
+}
+
 int read_device_status(void *stream, int *status)
 {
     int v = 0;

@@ -747,6 +747,120 @@ void emit_pass(Plan &plan, const std::vector<CGate> &gates, std::vector<int> S, 
     plan.passes.push_back(P);
 }
 
+// ------------------------------------------------------------------ tensor-core steps
+
+uint16_t bf16_rne(float f)
+{
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    u += 0x7FFFu + ((u >> 16) & 1u);
+    return uint16_t(u >> 16);
+}
+
+float bf16_value(uint16_t h)
+{
+    const uint32_t u = uint32_t(h) << 16;
+    float f;
+    std::memcpy(&f, &u, 4);
+    return f;
+}
+
+// Operand images of a 6-qubit gate U for the tensor-core kernel: the real embedding
+// E (128 x 128, rows = output index n, columns = input index k, interleaved re/im) split as
+// E = E_hi + E_lo in BF16 (from FP64), each stored in the 128-byte-swizzled K-major layout
+// (K split into 128-byte atoms of 64 elements stored one after the other for all 128 rows;
+// 16-byte chunk c of row r placed at chunk c ^ (r & 7)).
+void tc_images(const std::vector<cd> &U, std::vector<unsigned char> &out)
+{
+    const int K = kTcK, R = kTcK;
+    std::vector<uint16_t> hi(size_t(R) * K), lo(size_t(R) * K);
+    for (int j = 0; j < K / 2; ++j)
+        for (int l = 0; l < K / 2; ++l) {
+            const cd u = U[size_t(j) * (K / 2) + l];
+            const double e[2][2] = {{u.real(), -u.imag()}, {u.imag(), u.real()}};
+            for (int a = 0; a < 2; ++a)
+                for (int c = 0; c < 2; ++c) {
+                    const int n = 2 * j + a, k = 2 * l + c;
+                    const double x = e[a][c];
+                    const uint16_t h = bf16_rne((float)x);
+                    const uint16_t w = bf16_rne((float)(x - (double)bf16_value(h)));
+                    const size_t kb = size_t(k) >> 6, kin = size_t(k) & 63;
+                    const size_t chunk = kin >> 3, within = kin & 7;
+                    const size_t idx = kb * (size_t(R) * 64) + size_t(n) * 64 + ((chunk ^ (n & 7)) << 3) + within;
+                    hi[idx] = h;
+                    lo[idx] = w;
+                }
+        }
+    const size_t base = out.size();
+    out.resize(base + 2 * hi.size() * 2);
+    std::memcpy(out.data() + base, hi.data(), hi.size() * 2);
+    std::memcpy(out.data() + base + hi.size() * 2, lo.data(), lo.size() * 2);
+}
+
+// A tensor-core step for dense gate g (6 targets) at the current layout.
+void emit_tc(Plan &plan, const CGate &g, const std::vector<int> &phys, int lo, int n, int mode)
+{
+    std::set<int> S;
+    for (int p = 0; p < lo; ++p) S.insert(p);
+    for (int t : g.tq) S.insert(phys[t]);
+    for (int p = 0; (int)S.size() < kTcSlabBits && p < n; ++p) S.insert(p);
+    DevTc T;
+    std::memset(&T, 0, sizeof T);
+    std::vector<int> hi;
+    for (int p : S)
+        if (p >= lo) hi.push_back(p);
+    T.slab.b = (int)S.size();
+    T.slab.lo = lo;
+    T.slab.nhi = (int)hi.size();
+    for (size_t j = 0; j < hi.size(); ++j) T.slab.hipos[j] = (uint8_t)hi[j];
+    for (int j = 0; j < 32; ++j) T.slab.perm[j] = (uint8_t)j;
+    int local_of[64];
+    for (int p = 0; p < 64; ++p) local_of[p] = -1;
+    for (int p = 0; p < lo; ++p) local_of[p] = p;
+    for (size_t j = 0; j < hi.size(); ++j) local_of[hi[j]] = lo + (int)j;
+    uint32_t tmask = 0;
+    std::vector<int> tphys;
+    for (size_t j = 0; j < g.tq.size(); ++j) {
+        T.tpos[j] = (uint8_t)local_of[phys[g.tq[j]]];
+        tmask |= 1u << T.tpos[j];
+        tphys.push_back(phys[g.tq[j]]);
+    }
+    int m = 0;
+    for (int l = 0; l < kTcSlabBits; ++l)
+        if (!(tmask >> l & 1)) T.mpos[m++] = (uint8_t)l;
+    T.img = (uint32_t)plan.tc_images.size();
+    T.mode = mode;
+    tc_images(g.m, plan.tc_images);
+    plan.tc_coef.push_back((uint32_t)plan.coef.size());
+    plan.coef.insert(plan.coef.end(), g.m.begin(), g.m.end());
+    plan.tc_phys.push_back(tphys);
+    plan.steps.push_back({S_TC, (int)plan.tcs.size()});
+    plan.tcs.push_back(T);
+}
+
+// Widen a dense gate to 6 targets: identity on added qubits (added as the high index bits).
+CGate pad_to_tc(const CGate &g, int n, const std::vector<int> &phys)
+{
+    CGate r;
+    r.cls = C_DENSE;
+    r.tq = g.tq;
+    r.nsrc = g.nsrc;
+    // prefer qubits that already sit in the lowest physical positions
+    std::vector<int> byphys(n);
+    for (int q = 0; q < n; ++q) byphys[phys[q]] = q;
+    for (int p = 0; p < n && (int)r.tq.size() < kTcTargets; ++p) {
+        const int q = byphys[p];
+        if (std::find(r.tq.begin(), r.tq.end(), q) == r.tq.end()) r.tq.push_back(q);
+    }
+    const int k = (int)g.tq.size();
+    const size_t D = size_t(1) << kTcTargets, d = size_t(1) << k;
+    r.m.assign(D * D, 0.0);
+    for (size_t row = 0; row < D; ++row)
+        for (size_t col = 0; col < D; ++col)
+            if ((row >> k) == (col >> k)) r.m[row * D + col] = g.m[(row & (d - 1)) * d + (col & (d - 1))];
+    return r;
+}
+
 void emit_remap(Plan &plan, int n, int lo, const std::vector<int> &A, const std::vector<int> &B)
 {
     std::set<int> inS;
@@ -903,14 +1017,40 @@ int build_plan(const std::vector<CGate> &gates_in, int n, qs_dtype dt, const qs_
     };
 
     // ---- fusion (a fused dense gate must still fit one slab pass)
-    if (opt.fuse_width > 0) {
+    const bool tc = opt.tc != QS_TC_OFF;
+    if (tc) {
+        if (dt != QS_C64) {
+            err = "the tensor-core path is built for complex64 states";
+            return QS_EUNSUPPORTED;
+        }
+        if (opt.tc != QS_TC_BF16X3) {
+            err = "tensor-core mode: only BF16x3 splitting is built";
+            return QS_EUNSUPPORTED;
+        }
+        if (n < kTcSlabBits || !opt.blocking) {
+            err = "the tensor-core path needs blocking and at least 13 qubits";
+            return QS_EUNSUPPORTED;
+        }
+    }
+    std::vector<char> is_tc;
+    if (tc) {
+        // Alg. 2 level 3 with F = 6: merge greedily into dense blocks of at most 6 qubits; the
+        // products are FP64 on the host.  Blocks of 4+ qubits run on the tensor cores.
+        const int kdiag = opt.diag_bits > 0 ? std::min(opt.diag_bits, kMaxDiagBits) : 10;
+        gates = fuse_pass(gates, kdiag, 0, false, true, dt);
+        gates = fuse_pass(gates, kdiag, kTcTargets, true, false, dt);
+        for (const CGate &g : gates) is_tc.push_back(g.cls == C_DENSE && g.tq.size() >= 4);
+    } else if (opt.fuse_width > 0) {
         const int kdiag = opt.diag_bits > 0 ? std::min(opt.diag_bits, kMaxDiagBits) : 10;
         int kdense = std::min(opt.fuse_width, kMaxDense);
         if (opt.blocking) kdense = std::min(kdense, lowblock ? b : std::max(1, b - lo));
         gates = fuse_pass(gates, kdiag, 0, false, true, dt);
         gates = fuse_pass(gates, kdiag, kdense, false, false, dt);
     }
-    for (const CGate &g : gates) {
+    if (is_tc.empty()) is_tc.assign(gates.size(), 0);
+    for (size_t gi = 0; gi < gates.size(); ++gi) {
+        const CGate &g = gates[gi];
+        if (is_tc[gi]) continue;
         if (g.cls == C_DENSE && (int)g.tq.size() > kMaxDense) {
             err = "dense gates wider than 5 qubits need the tensor-core path";
             return QS_EUNSUPPORTED;
@@ -960,6 +1100,12 @@ int build_plan(const std::vector<CGate> &gates_in, int n, qs_dtype dt, const qs_
     while (true) {
         while (first < gates.size() && done[first]) ++first;
         if (first >= gates.size()) break;
+        if (is_tc[first]) {
+            emit_tc(plan, pad_to_tc(gates[first], n, phys), phys, lo, n, opt.tc);
+            done[first] = 1;
+            stalls = 0;
+            continue;
+        }
         std::set<int> S;
         for (int p = 0; p < (lowblock ? b : lo); ++p) S.insert(p);
         std::map<int, char> skipped;
@@ -968,7 +1114,7 @@ int build_plan(const std::vector<CGate> &gates_in, int n, qs_dtype dt, const qs_
         for (size_t i = first; i < gates.size(); ++i) {
             if (done[i]) continue;
             const CGate &g = gates[i];
-            if (!hoistable(g, skipped)) {
+            if (!hoistable(g, skipped) || is_tc[i]) {
                 note_skipped(g, skipped);
                 continue;
             }

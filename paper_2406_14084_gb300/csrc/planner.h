@@ -47,6 +47,10 @@ struct Plan {
     std::vector<DevOp> ops;
     std::vector<DevStage> stages;
     std::vector<DevSub> subs;
+    std::vector<DevTc> tcs;                 // tensor-core steps
+    std::vector<unsigned char> tc_images;   // their E_hi / E_lo operand images
+    std::vector<uint32_t> tc_coef;          // FP64 matrix of each tensor-core step (for listings)
+    std::vector<std::vector<int>> tc_phys;  // physical target positions of each step
     std::vector<cd> coef;        // matrices, tables and scalars, FP64
     std::vector<TcGate> tc;
     std::vector<int> final_phys_of;  // logical -> physical after the plan

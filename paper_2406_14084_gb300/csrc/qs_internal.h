@@ -104,6 +104,24 @@ struct DevStage {
 
 int num_sms();
 
+// Tensor-core wide gate (complex64 states).  A TC step is a slab pass over slabs of 2^13
+// amplitudes whose local bits are the 6 target bits (tpos, the K index of the GEMM) and 7 row
+// bits (mpos, the M index).  The operand images are the real embedding of the 64x64 unitary
+// split into hi and lo parts, pre-laid-out on the host in the 128-byte-swizzled K-major layout
+// of the tensor-core shared-memory descriptors.
+constexpr int kTcTargets = 6;
+constexpr int kTcSlabBits = 13;
+constexpr int kTcRows = 128;    // GEMM M per slab
+constexpr int kTcK = 128;       // real K = N = 2 * 2^6
+struct DevTc {
+    DevPass slab;                // slab definition (b = 13, lo, hipos); perm/op fields unused
+    uint8_t tpos[8];             // slab-local bit of target j (GEMM column bit j)
+    uint8_t mpos[8];             // slab-local bit of row-index bit j
+    uint32_t img;                // byte offset of this gate's operand images
+    int32_t mode;                // QS_TC_BF16X3 or QS_TC_TF32X3
+};
+size_t tc_image_bytes(int mode);  // bytes of the hi+lo B images of one gate
+
 // Launch entry points implemented in the .cu files (host side, stream-ordered).
 // `coef` points to the plan's coefficient pool already converted to the state precision.
 struct LaunchCtx {
@@ -125,6 +143,10 @@ int launch_pass(const LaunchCtx &c, const PassArgs &a, const DevPass &h_pass, ch
                 size_t errlen);
 // Device status word written by bounded waits that ran out (0 = fine).  Reading clears it.
 int read_device_status(void *stream, int *status);
+int *device_status_ptr();  // its device address on the current device
+
+int launch_tc(const LaunchCtx &c, const DevTc *d_tc, const DevTc &h_tc, const void *d_images,
+              char *err, size_t errlen);
 int launch_unblocked(const LaunchCtx &c, const DevOp *d_op, const DevOp &h_op,
                      const void *d_coef, char *err, size_t errlen);
 size_t pass_smem_bytes(qs_dtype dt, int b, int lo);

@@ -1,0 +1,70 @@
+"""Tensor-core path (complex64, BF16x3 split products, FP32 accumulate) against the FP64 oracle.
+
+The bar is infidelity <= 1e-6 (1 - |<psi_oracle|psi>|^2 / (|psi_oracle|^2 |psi|^2)); the largest
+amplitude error is reported and held to the complex64 tolerance of 1e-5.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2406_14084_gb300 import qs
+from paper_2406_14084_gb300 import workloads as W
+from paper_2406_14084_gb300.workloads import Gate
+
+pytestmark = pytest.mark.gpu
+
+
+def rand_state(n, seed):
+    rng = np.random.default_rng(seed)
+    v = rng.normal(size=1 << n) + 1j * rng.normal(size=1 << n)
+    return v / np.linalg.norm(v)
+
+
+def infidelity(a, b):
+    return 1.0 - abs(np.vdot(a, b)) ** 2 / (np.vdot(a, a).real * np.vdot(b, b).real)
+
+
+def run_tc(n, gates, init):
+    s = qs.State(n, qs.QS_C64)
+    try:
+        qs.qs_copy_from_host(s.h, init.astype(np.complex64))
+        s.apply(gates, qs.options(tc=qs.QS_TC_BF16X3, dtype=qs.QS_C64))
+        st = qs.qs_stats(s.h)
+        return s.amplitudes().astype(np.complex128), st
+    finally:
+        s.close()
+
+
+@pytest.mark.parametrize("targets", [(0, 1, 2, 3, 4, 5), (13, 2, 9, 0, 7, 4), (15, 14, 12, 11, 10, 8)])
+def test_single_six_qubit_unitary(targets):
+    n = 16
+    U = W.random_unitary(6, sum(targets))
+    gates = [Gate("UNITARY", targets, (), (), U)]
+    init = rand_state(n, 3)
+    want = oracle.apply_circuit(n, gates, init.copy())
+    got, st = run_tc(n, gates, init)
+    assert st["tc_gates"] == 1
+    assert infidelity(want, got) <= 1e-6
+    assert np.max(np.abs(got - want)) <= 1e-5
+
+
+@pytest.mark.parametrize("n,depth", [(14, 6), (17, 8)])
+def test_layered_circuit_on_tensor_cores(n, depth):
+    gates = W.layered(n, depth, 1003)
+    init = oracle.basis_state(n, 0)
+    want = oracle.apply_circuit(n, gates, init.copy())
+    got, st = run_tc(n, gates, init)
+    assert st["tc_gates"] > 0
+    assert infidelity(want, got) <= 1e-6
+    assert np.max(np.abs(got - want)) <= 1e-5
+
+
+def test_mixed_circuit_tc_and_simt_steps():
+    n = 15
+    gates = W.random_circuit(n, 150, 77, ["H", "T", "RZ", "U3", "CX", "CZ", "SWAP", "RY"]) + W.qft(n)
+    init = rand_state(n, 9)
+    want = oracle.apply_circuit(n, gates, init.copy())
+    got, st = run_tc(n, gates, init)
+    assert st["tc_gates"] > 0
+    assert infidelity(want, got) <= 1e-6
+    assert np.max(np.abs(got - want)) <= 1e-5

@@ -205,3 +205,22 @@ def test_fault_injection_on_host(monkeypatch):
     with pytest.raises(qs.QsError) as e:
         qs.qs_fuse([Gate("H", (0,))], 3)
     assert "injected" in str(e.value)
+
+
+@pytest.mark.parametrize("n", [13, 15])
+def test_tensor_core_plans_match_oracle(n):
+    """Tensor-core mode fuses into <= 6-qubit dense blocks (4+ qubit blocks padded to 6 run as
+    tensor-core steps); the listing carries the FP64 fused matrices, replayed on the oracle."""
+    gates = W.layered(n, 4, 11) + W.random_circuit(n, 40, 12, ALL)
+    info, stats = check_plan(gates, n, qs.options(tc=qs.QS_TC_BF16X3, dtype=qs.QS_C64))
+    assert info["tc_gates"] > 0
+
+
+def test_tensor_core_mode_rejections():
+    g = W.layered(14, 2, 1)
+    with pytest.raises(qs.QsError) as e:
+        qs.qs_fuse(g, 14, qs.options(tc=qs.QS_TC_BF16X3, dtype=qs.QS_C128))
+    assert e.value.status == qs.QS_EUNSUPPORTED
+    with pytest.raises(qs.QsError) as e:
+        qs.qs_fuse(W.layered(10, 2, 1), 10, qs.options(tc=qs.QS_TC_BF16X3, dtype=qs.QS_C64))
+    assert e.value.status == qs.QS_EUNSUPPORTED
