@@ -39,6 +39,8 @@ WORKLOADS = {
     "layered32_c128": dict(n=32, dtype="c128", kind="layered", depth=40, seed=1002),
     "qft32_c128": dict(n=32, dtype="c128", kind="qft", seed=1002),
     "layered30_c64": dict(n=30, dtype="c64", kind="layered", depth=40, seed=1002),
+    "precision33_c64": dict(n=33, dtype="c64", kind="layered", depth=60, seed=1003, tc=True),
+    "precision30_c64": dict(n=30, dtype="c64", kind="layered", depth=60, seed=1003, tc=True),
     "config1": dict(n=20, dtype="c128", kind="random", ngates=200, seed=1001),
 }
 
@@ -156,6 +158,27 @@ def oracle_sample(w, budget_s: float = 15.0):
 
 # ----------------------------------------------------------------------------- GPU leg
 
+def fidelity_check(w, opts, dtype, n_small=22):
+    """Same circuit family and options on an n_small-qubit state: GPU path vs the FP64 oracle."""
+    import numpy as np
+
+    import oracle
+    from paper_2406_14084_gb300 import qs
+
+    gates, x0 = make_circuit(w, n_small)
+    x0 &= (1 << n_small) - 1
+    want = oracle.apply_circuit(n_small, gates, oracle.basis_state(n_small, x0))
+    s = qs.State(n_small, dtype)
+    try:
+        s.set_basis(x0)
+        s.apply(gates, opts)
+        got = s.amplitudes().astype(np.complex128)
+    finally:
+        s.close()
+    ov = abs(np.vdot(want, got)) ** 2 / (np.vdot(want, want).real * np.vdot(got, got).real)
+    return {"qubits": n_small, "gates": len(gates), "infidelity": float(1.0 - ov),
+            "max_abs_err": float(np.max(np.abs(got - want))), "reference": "FP64 CPU oracle, same circuit family"}
+
 def run_gpu(args, w, ws, rank, local):
     import torch
 
@@ -184,6 +207,8 @@ def run_gpu(args, w, ws, rank, local):
         opts.seg_bits = args.seg_bits
     if w["kind"] == "random":
         opts.fuse_width, opts.blocking = 0, 0
+    if (w.get("tc") and args.tc != "off") or args.tc == "bf16x3":
+        opts.tc = qs.QS_TC_BF16X3
 
     t_plan0 = time.perf_counter()
     plan = qs.qs_fuse(gates, n, opts)
@@ -233,6 +258,7 @@ def run_gpu(args, w, ws, rank, local):
     peaks = measured_peaks()
     achieved = pass_bytes / (dom_ms / 1e3) / 1e9
     norm = qs.qs_norm2(state.h)
+    fidelity = None if args.no_fidelity else fidelity_check(w, opts, dtype)
 
     # ---- e2e through the public API with host inputs
     H = W.zz_chain_hamiltonian(n)
@@ -278,6 +304,8 @@ def run_gpu(args, w, ws, rank, local):
         "effective_frac_of_nominal_8tbs": eff_gbs / HBM_NOMINAL_GBS,
         "plan_s": t_plan,
         "norm_after": norm,
+        "fidelity": fidelity,
+        "tc": bool(opts.tc),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                      "frac": achieved / peaks["hbm_gbs"], "traffic": None,
                      "kernel": "slab_pass_kernel", "peak_source": peaks["source"],
@@ -301,6 +329,8 @@ def main():
     ap.add_argument("--slab-mode", default="gather", choices=["gather", "remap"])
     ap.add_argument("--stage-bits", type=int, default=0)
     ap.add_argument("--seg-bits", type=int, default=0)
+    ap.add_argument("--tc", default="auto", choices=["auto", "off", "bf16x3"])
+    ap.add_argument("--no-fidelity", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)

@@ -243,6 +243,48 @@ qs_status qs_probs_noalloc(const void *dev_amp, int n, qs_dtype dt, const int *q
 qs_status qs_expect_pauli_sum(qs_state *s, const qs_pauli_term *terms, size_t nterms,
                               double *host_out);
 
+/* ------------------------------------------------------------------------- batches */
+
+/* Many independent circuits of uneven qubit counts and depths simulated together.  Each
+ * circuit's gates are planned into slab passes as in qs_fuse (gather slabs); all passes of all
+ * circuits then run in ONE persistent kernel launch whose CTAs take (circuit, pass, slab)
+ * work items from a queue in dependency order, waiting (bounded) for a circuit's previous pass
+ * to be stored before starting its next one.  A circuit whose state fits one slab (n <= slab
+ * bits) runs entirely in shared memory.  The first pass prepares |0..0> in place; the last one
+ * also accumulates the circuit's expectation value.  qs_apply_batch replays the launch from a
+ * captured CUDA graph when options.graph is set.  Not in the paper (a library service). */
+typedef struct qs_batch qs_batch;
+
+typedef struct {
+    int32_t circuits;
+    int32_t items;          /* slab work items per run */
+    int32_t rounds;         /* passes of the deepest circuit */
+    int32_t slab_bits;      /* slab size limit in use */
+    int32_t stage_bits;     /* register-stage width in use */
+    int32_t graph;          /* 1 when runs replay a captured CUDA graph */
+    int64_t state_bytes;    /* device memory held for the circuits' states */
+    double last_run_ms;     /* device time of the last qs_apply_batch launch sequence */
+} qs_batch_info;
+
+/* Plan ncirc circuits (circuit c: n[c] qubits, gates[c][0..ngates[c]) ) and allocate their
+ * states on the current device.  options: dtype, slab_bits (0 = automatic), stage_bits,
+ * fuse_width and graph are honoured; blocking is always on and tc must be off.
+ * QS_ENOMEM if the states do not fit. */
+qs_status qs_batch_create(int ncirc, const int *n, const qs_gate *const *gates, const size_t *ngates,
+                          const qs_options *o, qs_batch **out);
+
+/* Run every circuit from |0..0> and write host_out[c] = sum_t coeff_t <psi_c|Z_t|psi_c> for the
+ * Z-string terms (xmask must be 0); a term with a Z bit at or above n[c] is left out for
+ * circuit c.  Synchronises.  QS_ETIMEOUT if a dependency wait ran out (results invalid). */
+qs_status qs_apply_batch(qs_batch *b, const qs_pauli_term *terms, size_t nterms, double *host_out);
+
+/* Autotuner: time the batch with each candidate (slab bits x stage width), keep the fastest.
+ * *chosen_slab_bits (may be NULL) receives the chosen slab size. */
+qs_status qs_batch_tune(qs_batch *b, const qs_pauli_term *terms, size_t nterms, int *chosen_slab_bits);
+
+qs_status qs_batch_info_get(const qs_batch *b, qs_batch_info *out);
+qs_status qs_batch_destroy(qs_batch *b);
+
 /* ------------------------------------------------------------------------- misc */
 
 qs_status qs_stats(qs_state *s, qs_stats_t *out);

@@ -46,6 +46,15 @@ qs_status cuda_status(cudaError_t e, const char *what)
 
 size_t amp_bytes(qs_dtype dt) { return dt == QS_C64 ? 8 : 16; }
 
+}  // namespace
+
+namespace qs {
+// Record an error for qs_last_error (used by the other host translation units).
+qs_status set_error(qs_status st, const std::string &msg) { return fail(st, msg); }
+}  // namespace qs
+
+namespace {
+
 struct DevPlanBuf {
     void *base = nullptr;
     DevPass *passes = nullptr;

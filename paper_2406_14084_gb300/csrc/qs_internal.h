@@ -147,6 +147,43 @@ int *device_status_ptr();  // its device address on the current device
 
 int launch_tc(const LaunchCtx &c, const DevTc *d_tc, const DevTc &h_tc, const void *d_images,
               char *err, size_t errlen);
+
+// Batched circuits (k_batch.cu).
+struct BatchCirc {
+    uint64_t amp_off;   // first amplitude of this circuit's state in the batch buffer
+    int32_t n, npass;   // qubits, slab passes
+    int32_t pass0;      // its first pass in the concatenated pass array
+    int32_t nslab_log;  // log2(slabs per pass)
+    int32_t term0, nterm;  // its Z terms (physical masks) in the term array
+    int32_t done0;      // its first per-pass done counter
+    int32_t pad;
+};
+struct BatchItem {
+    int32_t circ, pass;
+    uint32_t slab;
+    int32_t pad;
+};
+struct BatchTerm {
+    uint64_t zm;        // physical Z mask
+    double c;           // coefficient
+};
+struct BatchArgs {
+    const BatchCirc *circs;
+    const BatchItem *items;
+    unsigned nitems;
+    const DevPass *passes;
+    const DevOp *ops;
+    const DevStage *stages;
+    const DevSub *subs;
+    const void *coef;
+    const BatchTerm *terms;
+    unsigned *done;     // per circuit per pass: slabs stored (zeroed before each run)
+    unsigned *head;     // work-queue head (zeroed before each run)
+    double *results;    // per circuit expectation (zeroed before each run)
+    int *status;        // device status word
+};
+int launch_batch(qs_dtype dt, int stage_bits, void *states, const BatchArgs &a, int b_max, void *stream,
+                 char *err, size_t errlen);
 int launch_unblocked(const LaunchCtx &c, const DevOp *d_op, const DevOp &h_op,
                      const void *d_coef, char *err, size_t errlen);
 size_t pass_smem_bytes(qs_dtype dt, int b, int lo);

@@ -1,0 +1,416 @@
+// slab_common.cuh -- device code shared by the slab-pass kernel (k_slab.cu) and the batched
+// persistent kernel (k_batch.cu): PTX helpers and the register-stage sub-ops.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "dev_common.cuh"
+#include "qs_internal.h"
+
+namespace qs {
+
+
+namespace {
+
+constexpr uint32_t kWaitLimit = 1u << 24;  // mbarrier polls (with backoff) before giving up
+
+struct __align__(16) SlabShared {
+    uint64_t seg_lo[64];   // deposit of hi-bit index bits 0..5 into physical positions
+    uint64_t seg_hi[64];   // deposit of hi-bit index bits 6..11
+    uint16_t inv_lo[256];  // store permutation: source local index of destination bits 0..7
+    uint16_t inv_hi[256];  //                                    ... of destination bits 8..15
+    DevPass pass;
+    unsigned long long full[2];   // TMA load of buffer k has landed
+    unsigned long long empty[2];  // buffer k has been stored back and may be refilled
+};
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity)
+{
+    for (uint32_t i = 0; i < kWaitLimit; ++i) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (i > 64) __nanosleep(128);
+    }
+    return false;
+}
+
+// 1-D bulk copy global -> shared (TMA), completion counted on the mbarrier in bytes.
+__device__ __forceinline__ void tma_load_1d(uint32_t dst, const void *src, uint32_t bytes,
+                                            uint32_t bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            dst),
+        "l"(src), "r"(bytes), "r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void st_stream(uint4 *p, uint4 v)
+{
+    asm volatile("st.global.cs.v4.u32 [%0], {%1,%2,%3,%4};" ::"l"(p), "r"(v.x), "r"(v.y),
+                 "r"(v.z), "r"(v.w)
+                 : "memory");
+}
+
+// ------------------------------------------------------------------ register sub-ops
+
+template <typename C, int RB, int J, bool CTL>
+__device__ __forceinline__ void sub_g1_impl(C (&v)[1 << RB], const C *__restrict__ M, uint32_t scm)
+{
+    const C m00 = M[0], m01 = M[1], m10 = M[2], m11 = M[3];
+#pragma unroll
+    for (int e = 0; e < (1 << RB); ++e) {
+        if (e & (1 << J)) continue;
+        if (CTL && (uint32_t(e) & scm) != scm) continue;
+        const int e1 = e | (1 << J);
+        const C a = v[e], b = v[e1];
+        v[e] = cmac(m01, b, cmul(m00, a));
+        v[e1] = cmac(m11, b, cmul(m10, a));
+    }
+}
+
+template <typename C, int RB, int J>
+__device__ __forceinline__ void sub_g1(C (&v)[1 << RB], const C *__restrict__ M, uint32_t scm)
+{
+    if (scm == 0) sub_g1_impl<C, RB, J, false>(v, M, 0);
+    else sub_g1_impl<C, RB, J, true>(v, M, scm);
+}
+
+template <typename C, int RB, int J0, int J1, bool CTL>
+__device__ __forceinline__ void sub_g2_impl(C (&v)[1 << RB], const C *__restrict__ M, uint32_t scm)
+{
+#pragma unroll
+    for (int e = 0; e < (1 << RB); ++e) {
+        if (e & ((1 << J0) | (1 << J1))) continue;
+        if (CTL && (uint32_t(e) & scm) != scm) continue;
+        const int i0 = e, i1 = e | (1 << J0), i2 = e | (1 << J1), i3 = e | (1 << J0) | (1 << J1);
+        const C a0 = v[i0], a1 = v[i1], a2 = v[i2], a3 = v[i3];
+        C r[4];
+#pragma unroll
+        for (int row = 0; row < 4; ++row) {
+            C acc = cmul(M[row * 4 + 0], a0);
+            acc = cmac(M[row * 4 + 1], a1, acc);
+            acc = cmac(M[row * 4 + 2], a2, acc);
+            acc = cmac(M[row * 4 + 3], a3, acc);
+            r[row] = acc;
+        }
+        v[i0] = r[0];
+        v[i1] = r[1];
+        v[i2] = r[2];
+        v[i3] = r[3];
+    }
+}
+
+template <typename C, int RB, int J0, int J1>
+__device__ __forceinline__ void sub_g2(C (&v)[1 << RB], const C *__restrict__ M, uint32_t scm)
+{
+    if (scm == 0) sub_g2_impl<C, RB, J0, J1, false>(v, M, 0);
+    else sub_g2_impl<C, RB, J0, J1, true>(v, M, scm);
+}
+
+// Phase p on the elements whose bits MASK are all set (MASK is a compile-time constant).
+template <typename C, int RB, int MASK, int UNUSED>
+__device__ __forceinline__ void sub_phase_mask(C (&v)[1 << RB], C p, bool neg)
+{
+    if (neg) {
+#pragma unroll
+        for (int e = 0; e < (1 << RB); ++e)
+            if ((e & MASK) == MASK) {
+                v[e].x = -v[e].x;
+                v[e].y = -v[e].y;
+            }
+    } else {
+#pragma unroll
+        for (int e = 0; e < (1 << RB); ++e)
+            if ((e & MASK) == MASK) v[e] = cmul(p, v[e]);
+    }
+}
+
+// 2x2 matrix with real entries (H, RY, ...): half the arithmetic of the complex case.
+template <typename C, int RB, int J, bool CTL>
+__device__ __forceinline__ void sub_g1r_impl(C (&v)[1 << RB], const C *__restrict__ M, uint32_t scm)
+{
+    const auto m00 = M[0].x, m01 = M[1].x, m10 = M[2].x, m11 = M[3].x;
+#pragma unroll
+    for (int e = 0; e < (1 << RB); ++e) {
+        if (e & (1 << J)) continue;
+        if (CTL && (uint32_t(e) & scm) != scm) continue;
+        const int e1 = e | (1 << J);
+        const C a = v[e], b = v[e1];
+        v[e].x = fma(m01, b.x, m00 * a.x);
+        v[e].y = fma(m01, b.y, m00 * a.y);
+        v[e1].x = fma(m11, b.x, m10 * a.x);
+        v[e1].y = fma(m11, b.y, m10 * a.y);
+    }
+}
+
+template <typename C, int RB, int J>
+__device__ __forceinline__ void sub_g1r(C (&v)[1 << RB], const C *__restrict__ M, uint32_t scm)
+{
+    if (scm == 0) sub_g1r_impl<C, RB, J, false>(v, M, 0);
+    else sub_g1r_impl<C, RB, J, true>(v, M, scm);
+}
+
+template <typename C, int RB, int J>
+__device__ __forceinline__ void sub_x(C (&v)[1 << RB], uint32_t scm)
+{
+#pragma unroll
+    for (int e = 0; e < (1 << RB); ++e) {
+        if (e & (1 << J)) continue;
+        if ((uint32_t(e) & scm) != scm) continue;
+        const C t = v[e];
+        v[e] = v[e | (1 << J)];
+        v[e | (1 << J)] = t;
+    }
+}
+
+template <typename C, int RB, int J0, int J1>
+__device__ __forceinline__ void sub_swap(C (&v)[1 << RB], uint32_t scm)
+{
+#pragma unroll
+    for (int e = 0; e < (1 << RB); ++e) {
+        // elements with bit J0 = 1, bit J1 = 0 exchange with bit J0 = 0, bit J1 = 1
+        if (!(e & (1 << J0)) || (e & (1 << J1))) continue;
+        if ((uint32_t(e) & scm) != scm) continue;
+        const int f = e ^ ((1 << J0) | (1 << J1));
+        const C t = v[e];
+        v[e] = v[f];
+        v[f] = t;
+    }
+}
+
+template <typename C, int RB>
+__device__ __forceinline__ void apply_sub(C (&v)[1 << RB], const DevSub &s, uint32_t gbase,
+                                          uint64_t cta_base, const C *__restrict__ coef)
+{
+    if ((gbase & s.lcm) != s.lcm || (cta_base & s.ocm) != s.ocm) return;
+    const C *__restrict__ M = coef + s.mat;
+    const uint32_t scm = s.scm;
+    switch (s.type) {
+    case SB_G1:
+        switch (s.j0) {
+        case 0: sub_g1<C, RB, 0>(v, M, scm); break;
+        case 1: sub_g1<C, RB, 1>(v, M, scm); break;
+        case 2: sub_g1<C, RB, 2>(v, M, scm); break;
+        case 3: sub_g1<C, RB, 3>(v, M, scm); break;
+        case 4: if (RB > 4) sub_g1<C, RB, (RB > 4 ? 4 : 0)>(v, M, scm); break;
+        default: break;
+        }
+        break;
+    case SB_G2:
+        switch (s.j0 * 8 + s.j1) {
+        case 0 * 8 + 1: sub_g2<C, RB, 0, 1>(v, M, scm); break;
+        case 0 * 8 + 2: sub_g2<C, RB, 0, 2>(v, M, scm); break;
+        case 0 * 8 + 3: sub_g2<C, RB, 0, 3>(v, M, scm); break;
+        case 1 * 8 + 2: sub_g2<C, RB, 1, 2>(v, M, scm); break;
+        case 1 * 8 + 3: sub_g2<C, RB, 1, 3>(v, M, scm); break;
+        case 2 * 8 + 3: sub_g2<C, RB, 2, 3>(v, M, scm); break;
+        case 0 * 8 + 4: if (RB > 4) sub_g2<C, RB, 0, (RB > 4 ? 4 : 1)>(v, M, scm); break;
+        case 1 * 8 + 4: if (RB > 4) sub_g2<C, RB, 1, (RB > 4 ? 4 : 2)>(v, M, scm); break;
+        case 2 * 8 + 4: if (RB > 4) sub_g2<C, RB, 2, (RB > 4 ? 4 : 3)>(v, M, scm); break;
+        case 3 * 8 + 4: if (RB > 4) sub_g2<C, RB, 3, (RB > 4 ? 4 : 0)>(v, M, scm); break;
+        default: break;
+        }
+        break;
+    case SB_X:
+        switch (s.j0) {
+        case 0: sub_x<C, RB, 0>(v, scm); break;
+        case 1: sub_x<C, RB, 1>(v, scm); break;
+        case 2: sub_x<C, RB, 2>(v, scm); break;
+        case 3: sub_x<C, RB, 3>(v, scm); break;
+        case 4: if (RB > 4) sub_x<C, RB, (RB > 4 ? 4 : 0)>(v, scm); break;
+        default: break;
+        }
+        break;
+    case SB_SWAP:
+        switch (s.j0 * 8 + s.j1) {
+        case 0 * 8 + 1: sub_swap<C, RB, 0, 1>(v, scm); break;
+        case 0 * 8 + 2: sub_swap<C, RB, 0, 2>(v, scm); break;
+        case 0 * 8 + 3: sub_swap<C, RB, 0, 3>(v, scm); break;
+        case 1 * 8 + 2: sub_swap<C, RB, 1, 2>(v, scm); break;
+        case 1 * 8 + 3: sub_swap<C, RB, 1, 3>(v, scm); break;
+        case 2 * 8 + 3: sub_swap<C, RB, 2, 3>(v, scm); break;
+        case 0 * 8 + 4: if (RB > 4) sub_swap<C, RB, 0, (RB > 4 ? 4 : 1)>(v, scm); break;
+        case 1 * 8 + 4: if (RB > 4) sub_swap<C, RB, 1, (RB > 4 ? 4 : 2)>(v, scm); break;
+        case 2 * 8 + 4: if (RB > 4) sub_swap<C, RB, 2, (RB > 4 ? 4 : 3)>(v, scm); break;
+        case 3 * 8 + 4: if (RB > 4) sub_swap<C, RB, 3, (RB > 4 ? 4 : 0)>(v, scm); break;
+        default: break;
+        }
+        break;
+    case SB_PHASE: {
+        // Only the elements whose masked register bits are all 1 change.  Masks of 0, 1 or 2
+        // register bits (Z/S/T/P, CZ/CP) get compile-time element lists, so no arithmetic is
+        // issued for the untouched elements (predicated-off FP64 work still occupies the
+        // narrow FP64 pipe).
+        const C p = M[0];
+        const bool neg = (p.x == -1 && p.y == 0);
+        const int pc = __popc(scm);
+        if (pc == 0) {
+            sub_phase_mask<C, RB, 0, 0>(v, p, neg);
+        } else if (pc == 1) {
+            switch (__ffs(scm) - 1) {
+            case 0: sub_phase_mask<C, RB, 1, 0>(v, p, neg); break;
+            case 1: sub_phase_mask<C, RB, 2, 0>(v, p, neg); break;
+            case 2: sub_phase_mask<C, RB, 4, 0>(v, p, neg); break;
+            case 3: sub_phase_mask<C, RB, 8, 0>(v, p, neg); break;
+            case 4: sub_phase_mask<C, RB, (RB > 4 ? 16 : 1), 0>(v, p, neg); break;
+            default: break;
+            }
+        } else if (pc == 2) {
+            switch (scm) {
+            case 0x03: sub_phase_mask<C, RB, 0x03, 0>(v, p, neg); break;
+            case 0x05: sub_phase_mask<C, RB, 0x05, 0>(v, p, neg); break;
+            case 0x06: sub_phase_mask<C, RB, 0x06, 0>(v, p, neg); break;
+            case 0x09: sub_phase_mask<C, RB, 0x09, 0>(v, p, neg); break;
+            case 0x0a: sub_phase_mask<C, RB, 0x0a, 0>(v, p, neg); break;
+            case 0x0c: sub_phase_mask<C, RB, 0x0c, 0>(v, p, neg); break;
+            case 0x11: sub_phase_mask<C, RB, (RB > 4 ? 0x11 : 0x03), 0>(v, p, neg); break;
+            case 0x12: sub_phase_mask<C, RB, (RB > 4 ? 0x12 : 0x03), 0>(v, p, neg); break;
+            case 0x14: sub_phase_mask<C, RB, (RB > 4 ? 0x14 : 0x03), 0>(v, p, neg); break;
+            case 0x18: sub_phase_mask<C, RB, (RB > 4 ? 0x18 : 0x03), 0>(v, p, neg); break;
+            default: break;
+            }
+        } else {
+#pragma unroll
+            for (int e = 0; e < (1 << RB); ++e)
+                if ((uint32_t(e) & scm) == scm) v[e] = cmul(p, v[e]);
+        }
+        break;
+    }
+    case SB_G1R:
+        switch (s.j0) {
+        case 0: sub_g1r<C, RB, 0>(v, M, scm); break;
+        case 1: sub_g1r<C, RB, 1>(v, M, scm); break;
+        case 2: sub_g1r<C, RB, 2>(v, M, scm); break;
+        case 3: sub_g1r<C, RB, 3>(v, M, scm); break;
+        case 4: if (RB > 4) sub_g1r<C, RB, (RB > 4 ? 4 : 0)>(v, M, scm); break;
+        default: break;
+        }
+        break;
+    case SB_DIAG: {
+        uint32_t hi = 0;
+        for (int j = 0; j < s.ndl; ++j) {
+            const uint32_t src = s.dl[j];
+            const uint32_t bit = (src & 0x80) ? uint32_t((cta_base >> (src & 0x7f)) & 1)
+                                              : ((gbase >> src) & 1u);
+            hi |= bit << j;
+        }
+        const C *__restrict__ T = M + (size_t(hi) << RB);
+#pragma unroll
+        for (int e = 0; e < (1 << RB); ++e) v[e] = cmul(__ldg(&T[e]), v[e]);
+        break;
+    }
+    default: break;
+    }
+}
+
+template <typename C, int RB>
+__device__ __noinline__ void run_stage(C *sm, const DevStage *__restrict__ stg,
+                                          const DevSub *__restrict__ subs, const C *__restrict__ coef,
+                                          uint64_t cta_base, uint32_t tid, uint32_t nthr)
+{
+    constexpr int E = 1 << RB;
+    const int nrest = stg->nrest;
+    const uint32_t ngroups = 1u << nrest;
+    const int s0 = stg->sub_begin, s1 = stg->sub_end;
+    for (uint32_t g = tid; g < ngroups; g += nthr) {
+        uint32_t base = 0;
+        for (int j = 0; j < nrest; ++j) base |= ((g >> j) & 1u) << stg->rest[j];
+        // off[e] holds swizzled offsets; the swizzle is linear, so one XOR per element
+        const uint32_t pb = swz<(sizeof(C) == 8 ? 1 : 2)>(base);
+        C v[E];
+#pragma unroll
+        for (int e = 0; e < E; ++e) v[e] = sm[pb ^ stg->off[e]];
+        for (int s = s0; s < s1; ++s) apply_sub<C, RB>(v, subs[s], base, cta_base, coef);
+#pragma unroll
+        for (int e = 0; e < E; ++e) sm[pb ^ stg->off[e]] = v[e];
+    }
+}
+
+// Ops applied directly to the shared-memory slab, kept out of line so that their register
+// needs do not compete with the register stage's amplitude array.
+template <typename C>
+__device__ __noinline__ void run_smem_op(C *sm, int b, const DevOp &op, const C *__restrict__ coef,
+                                         uint64_t base, uint32_t tid, uint32_t nthr)
+{
+    uint32_t toff = 0;
+    if (op.type == OP_DIAG)
+        for (int j = 0; j < op.nout; ++j) toff |= uint32_t((base >> op.outpos[j]) & 1) << (op.k + j);
+    apply_op<C, uint32_t, (sizeof(C) == 8 ? 1 : 2)>(sm, b, op, coef, toff, tid, nthr);
+}
+
+// Named barrier 1 among the NT compute threads (the producer warp never joins it).
+__device__ __forceinline__ void compute_sync(uint32_t nthreads)
+{
+    asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory");
+}
+
+// OR of a predicate over the NT compute threads (also a barrier).
+__device__ __forceinline__ bool compute_any(bool v, uint32_t nthreads)
+{
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 p, %1, 0;\n\t"
+        "bar.red.or.pred q, 1, %2, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"(uint32_t(v)), "r"(nthreads)
+        : "memory");
+    return r != 0;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// 16-byte asynchronous global -> shared copies (L2 only, no L1 allocation).
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+}  // namespace
+}  // namespace qs

@@ -66,6 +66,12 @@ class QsPlanInfo(ctypes.Structure):
                 ("stage_bits", ctypes.c_int32)]
 
 
+class QsBatchInfo(ctypes.Structure):
+    _fields_ = [("circuits", ctypes.c_int32), ("items", ctypes.c_int32), ("rounds", ctypes.c_int32),
+                ("slab_bits", ctypes.c_int32), ("stage_bits", ctypes.c_int32), ("graph", ctypes.c_int32),
+                ("state_bytes", ctypes.c_int64), ("last_run_ms", ctypes.c_double)]
+
+
 class QsStats(ctypes.Structure):
     _fields_ = [("passes", ctypes.c_int64), ("remaps", ctypes.c_int64), ("unblocked", ctypes.c_int64),
                 ("tc_gates", ctypes.c_int64), ("plans_applied", ctypes.c_int64),
@@ -106,6 +112,12 @@ _SIGS = {
     "qs_stats": [_vp, ctypes.POINTER(QsStats)],
     "qs_stats_reset": [_vp],
     "qs_set_profiling": [_vp, _i],
+    "qs_batch_create": [_i, ctypes.POINTER(_i), ctypes.POINTER(ctypes.POINTER(QsGate)),
+                        ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(QsOptions), ctypes.POINTER(_vp)],
+    "qs_apply_batch": [_vp, ctypes.POINTER(QsPauliTerm), ctypes.c_size_t, _dp],
+    "qs_batch_tune": [_vp, ctypes.POINTER(QsPauliTerm), ctypes.c_size_t, ctypes.POINTER(_i)],
+    "qs_batch_info_get": [_vp, ctypes.POINTER(QsBatchInfo)],
+    "qs_batch_destroy": [_vp],
     "qs_last_error": [],
     "qs_version": [],
 }
@@ -328,6 +340,56 @@ def qs_expect_pauli_sum(state, terms) -> complex:
     out = (ctypes.c_double * 2)()
     _check(lib().qs_expect_pauli_sum(state, arr, nt, out))
     return complex(out[0], out[1])
+
+
+def _terms_array(terms):
+    nt = len(terms)
+    arr = (QsPauliTerm * max(1, nt))()
+    for i, (c, x, z) in enumerate(terms):
+        arr[i].coeff, arr[i].xmask, arr[i].zmask = float(c), int(x), int(z)
+    return arr, nt
+
+
+def qs_batch_create(circuits, opts: QsOptions | None = None):
+    """circuits: list of (n, gates).  Returns a batch handle."""
+    nc = len(circuits)
+    ns = (_i * nc)(*[c[0] for c in circuits])
+    keep = []
+    ptrs = (ctypes.POINTER(QsGate) * nc)()
+    counts = (ctypes.c_size_t * nc)()
+    for i, (n, gates) in enumerate(circuits):
+        arr, k = marshal_gates(gates)
+        keep.append((arr, k))
+        ptrs[i] = ctypes.cast(arr, ctypes.POINTER(QsGate))
+        counts[i] = len(gates)
+    h = _vp()
+    _check(lib().qs_batch_create(nc, ns, ptrs, counts, ctypes.byref(opts) if opts is not None else None,
+                                 ctypes.byref(h)))
+    return h
+
+
+def qs_apply_batch(batch, terms, ncirc: int) -> np.ndarray:
+    arr, nt = _terms_array(terms)
+    out = np.empty(ncirc, dtype=np.float64)
+    _check(lib().qs_apply_batch(batch, arr, nt, out.ctypes.data_as(_dp)))
+    return out
+
+
+def qs_batch_tune(batch, terms) -> int:
+    arr, nt = _terms_array(terms)
+    chosen = _i()
+    _check(lib().qs_batch_tune(batch, arr, nt, ctypes.byref(chosen)))
+    return chosen.value
+
+
+def qs_batch_info_get(batch) -> dict:
+    info = QsBatchInfo()
+    _check(lib().qs_batch_info_get(batch, ctypes.byref(info)))
+    return {f: getattr(info, f) for f, _ in QsBatchInfo._fields_}
+
+
+def qs_batch_destroy(batch):
+    _check(lib().qs_batch_destroy(batch))
 
 
 def qs_stats(state) -> dict:
