@@ -42,6 +42,8 @@ WORKLOADS = {
     "precision33_c64": dict(n=33, dtype="c64", kind="layered", depth=60, seed=1003, tc=True),
     "precision30_c64": dict(n=30, dtype="c64", kind="layered", depth=60, seed=1003, tc=True),
     "config1": dict(n=20, dtype="c128", kind="random", ngates=200, seed=1001),
+    "batch1024_c64": dict(n=24, dtype="c64", kind="batch", count=1024, seed=1004),
+    "batch1024_c128": dict(n=24, dtype="c128", kind="batch", count=1024, seed=1004),
 }
 
 
@@ -136,6 +138,9 @@ def oracle_sample(w, budget_s: float = 15.0):
 
     import oracle
 
+    if w["kind"] == "batch":
+        return oracle_sample_batch(w, budget_s)
+
     n_full = w["n"]
     n_s = min(n_full, 25)
     gates, x0 = make_circuit(w, n_s)
@@ -155,6 +160,95 @@ def oracle_sample(w, budget_s: float = 15.0):
             "sample": f"first {done} gates of the same circuit family on a {n_s}-qubit complex128 "
                       f"state in {dt:.1f} s, gates/s scaled by 2^({n_s}-{n_full})"}
 
+
+def oracle_sample_batch(w, budget_s: float):
+    """Oracle amplitude-gate rate on the batch's smallest circuits, scaled to the whole batch."""
+    import oracle
+    from paper_2406_14084_gb300 import workloads as W
+
+    circuits = W.vqe_batch(w["count"], w["seed"])
+    total_gates = sum(len(g) for _, g in circuits)
+    total_work = sum(len(g) * (1 << n) for n, g in circuits)
+    done_work, done_c, t0 = 0, 0, time.perf_counter()
+    for n, g in sorted(circuits, key=lambda c: c[0]):
+        a = oracle.apply_circuit(n, g)
+        oracle.expect_pauli(a, n, W.zz_chain_hamiltonian(n))
+        done_work += len(g) * (1 << n)
+        done_c += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    est = total_work / (done_work / dt)
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": total_gates / est, "unit": "gates/s", "cores": cores, "kind": "oracle",
+            "sample": f"{done_c} smallest circuits of the batch (with <H>) in {dt:.1f} s; rate of "
+                      f"amplitude-gate updates scaled to all {len(circuits)} circuits"}
+
+
+def run_batch(args, w):
+    """Batched persistent launch over the whole circuit list (one graph replay per step)."""
+    import torch
+
+    from paper_2406_14084_gb300 import qs
+    from paper_2406_14084_gb300 import workloads as W
+
+    torch.cuda.set_device(0)
+    dtype = qs.QS_C64 if w["dtype"] == "c64" else qs.QS_C128
+    circuits = W.vqe_batch(w["count"], w["seed"])
+    H = W.zz_chain_hamiltonian(24)
+    ngates = sum(len(g) for _, g in circuits)
+    t_plan0 = time.perf_counter()
+    b = qs.qs_batch_create(circuits, qs.options(dtype=dtype, graph=1))
+    t_plan = time.perf_counter() - t_plan0
+    chosen = qs.qs_batch_tune(b, H)
+    for _ in range(args.warmup):
+        qs.qs_apply_batch(b, H, len(circuits))
+    clocks = ClockSampler(0)
+    clocks.start()
+    dev_ms, t0 = 0.0, time.perf_counter()
+    for _ in range(args.steps):
+        res = qs.qs_apply_batch(b, H, len(circuits))
+        dev_ms += qs.qs_batch_info_get(b)["last_run_ms"]
+    wall = time.perf_counter() - t0
+    clk = clocks.stop()
+    info = qs.qs_batch_info_get(b)
+    qs.qs_batch_destroy(b)
+    # e2e: the user's whole call sequence -- create (planning, plan upload), run, read back <H>
+    e2e_t0 = time.perf_counter()
+    b2 = qs.qs_batch_create(circuits, qs.options(dtype=dtype, graph=0, slab_bits=chosen))
+    qs.qs_apply_batch(b2, H, len(circuits))
+    e2e_s = time.perf_counter() - e2e_t0
+    kept_terms = sum(sum(1 for t in H if t[2] < (1 << n)) for n, _ in circuits)
+    e2e_h2d = qs.qs_batch_info_get(b2)["plan_bytes"] + 16 * kept_terms + 40 * len(circuits)
+    qs.qs_batch_destroy(b2)
+    # the plain form: one qs_apply_circuit + qs_expect_pauli_sum per circuit, same GPU
+    p0 = time.perf_counter()
+    plain = []
+    for n, g in circuits:
+        st = qs.State(n, dtype)
+        st.apply(g, qs.options(dtype=dtype))
+        plain.append(st.expect(W.zz_chain_hamiltonian(n)).real)
+        st.close()
+    plain_s = time.perf_counter() - p0
+    import numpy as np
+    agree = float(np.max(np.abs(np.array(plain) - res)))
+    ms_step = dev_ms / args.steps
+    return {
+        "metric": "gates/s", "value": ngates / (ms_step / 1e3), "unit": "gates/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": w["dtype"],
+        "data": "synthetic (seeded hardware-efficient ansatz batch)",
+        "config": {"workload": args.workload, "circuits": len(circuits), "gates": ngates,
+                   "qubits": "10..24", "layers": "2..12", "items": info["items"], "rounds": info["rounds"],
+                   "slab_bits": chosen, "stage_bits": info["stage_bits"], "graph": True,
+                   "state_bytes": info["state_bytes"], "l2": "states larger than L2"},
+        "wall_ms_per_step": 1e3 * wall / args.steps, "plan_s": t_plan,
+        "plain_form": {"gates_per_s": ngates / plain_s, "seconds": plain_s,
+                       "max_abs_diff_vs_batched": agree},
+        "clocks": clk, "gpu_launches": args.steps,
+        "e2e": {"value": ngates / e2e_s, "unit": "gates/s", "h2d_bytes_per_step": int(e2e_h2d),
+                "d2h_bytes_per_step": 8 * len(circuits)},
+    }
 
 # ----------------------------------------------------------------------------- GPU leg
 
@@ -360,7 +454,12 @@ def main():
         }))
         return
 
-    line = run_gpu(args, w, ws, rank, local)
+    if w["kind"] == "batch":
+        if rank != 0:
+            return
+        line = run_batch(args, w)
+    else:
+        line = run_gpu(args, w, ws, rank, local)
     if line is None:
         return
     if not args.no_cpu_baseline and ws == 1:

@@ -264,6 +264,7 @@ typedef struct {
     int32_t graph;          /* 1 when runs replay a captured CUDA graph */
     int64_t state_bytes;    /* device memory held for the circuits' states */
     double last_run_ms;     /* device time of the last qs_apply_batch launch sequence */
+    int64_t plan_bytes;     /* host-to-device bytes of the plan upload (ops, stages, items, tables) */
 } qs_batch_info;
 
 /* Plan ncirc circuits (circuit c: n[c] qubits, gates[c][0..ngates[c]) ) and allocate their

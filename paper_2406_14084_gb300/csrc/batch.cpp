@@ -40,6 +40,7 @@ struct qs_batch {
     // device memory
     void *states = nullptr;
     size_t state_bytes = 0;
+    size_t plan_bytes = 0;
     void *buf = nullptr;  // plan arrays, circuits, items
     BatchArgs args{};
     void *terms_buf = nullptr;
@@ -206,6 +207,7 @@ qs_status build(qs_batch *B, int slab_bits, int stage_bits)
     if (st) return st;
     st = cuda_err(cudaMemcpy(B->buf, h.data(), h.size(), cudaMemcpyHostToDevice), "batch plan upload");
     if (st) return st;
+    B->plan_bytes = h.size();
     const size_t ctl_bytes = ((size_t(B->ndone) + 1) * sizeof(unsigned) + 255) / 256 * 256 + B->ncirc * sizeof(double);
     st = cuda_err(cudaMalloc(&B->ctl, ctl_bytes), "batch control allocation");
     if (st) return st;
@@ -445,6 +447,7 @@ qs_status qs_batch_info_get(const qs_batch *b, qs_batch_info *out)
     out->graph = b->opt.graph ? 1 : 0;
     out->state_bytes = (int64_t)b->state_bytes;
     out->last_run_ms = b->last_ms;
+    out->plan_bytes = (int64_t)b->plan_bytes;
     return QS_OK;
 }
 

@@ -69,7 +69,8 @@ class QsPlanInfo(ctypes.Structure):
 class QsBatchInfo(ctypes.Structure):
     _fields_ = [("circuits", ctypes.c_int32), ("items", ctypes.c_int32), ("rounds", ctypes.c_int32),
                 ("slab_bits", ctypes.c_int32), ("stage_bits", ctypes.c_int32), ("graph", ctypes.c_int32),
-                ("state_bytes", ctypes.c_int64), ("last_run_ms", ctypes.c_double)]
+                ("state_bytes", ctypes.c_int64), ("last_run_ms", ctypes.c_double),
+                ("plan_bytes", ctypes.c_int64)]
 
 
 class QsStats(ctypes.Structure):
