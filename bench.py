@@ -44,6 +44,8 @@ WORKLOADS = {
     "config1": dict(n=20, dtype="c128", kind="random", ngates=200, seed=1001),
     "batch1024_c64": dict(n=24, dtype="c64", kind="batch", count=1024, seed=1004),
     "batch1024_c128": dict(n=24, dtype="c128", kind="batch", count=1024, seed=1004),
+    "learned32_c128": dict(n=32, dtype="c128", kind="learned", depth=80, seed=1005),
+    "learned28_c128": dict(n=28, dtype="c128", kind="learned", depth=80, seed=1005),
 }
 
 
@@ -51,7 +53,7 @@ def make_circuit(w, n=None):
     from paper_2406_14084_gb300 import workloads as W
 
     n = n or w["n"]
-    if w["kind"] == "layered":
+    if w["kind"] in ("layered", "learned"):
         return W.layered(n, w["depth"], w["seed"]), 0
     if w["kind"] == "qft":
         return W.qft(n), W.random_basis(n, w["seed"])
@@ -248,6 +250,69 @@ def run_batch(args, w):
         "clocks": clk, "gpu_launches": args.steps,
         "e2e": {"value": ngates / e2e_s, "unit": "gates/s", "h2d_bytes_per_step": int(e2e_h2d),
                 "d2h_bytes_per_step": 8 * len(circuits)},
+    }
+
+def run_learned(args, w):
+    """Learned planner against greedy on the same GPU: layered depth-80 and QFT circuits.
+
+    Each circuit is planned twice (greedy = the caller's options; learned = the shipped cost
+    model), both plans run on the same resident state, and each step is the sum over the two
+    circuits of the plan's device time (CUDA events around every launch)."""
+    import numpy as np
+    import torch
+
+    from paper_2406_14084_gb300 import costmodel
+    from paper_2406_14084_gb300 import qs
+    from paper_2406_14084_gb300 import workloads as W
+
+    torch.cuda.set_device(0)
+    dtype = qs.QS_C64 if w["dtype"] == "c64" else qs.QS_C128
+    n = w["n"]
+    circuits = [("layered", W.layered(n, w["depth"], w["seed"])), ("qft", W.qft(n))]
+    model = costmodel.load(os.path.join(ROOT, "paper_2406_14084_gb300", "data", "cost_model.npz"))
+    st = qs.State(n, dtype)
+    rows, ms = {}, {"greedy": 0.0, "learned": 0.0}
+    launches = 0
+    clocks = ClockSampler(0)
+    for name, g in circuits:
+        t0 = time.perf_counter()
+        pg = qs.qs_fuse(g, n, qs.options(dtype=dtype))
+        tg = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        pl = qs.qs_fuse_learned(g, n, qs.options(dtype=dtype), model)
+        tl = time.perf_counter() - t0
+        info = qs.qs_plan_info_get(pl)
+        res = {"gates": len(g), "plan_s_greedy": tg, "plan_s_learned": tl, "candidates": info["candidates"],
+               "chosen": info["chosen"], "predicted_ms": info["predicted_ms"],
+               "greedy_predicted_ms": info["greedy_predicted_ms"]}
+        for tag, p in (("greedy", pg), ("learned", pl)):
+            steps = qs.qs_plan_features(p).shape[0]
+            for _ in range(args.warmup):
+                qs.qs_plan_profile(st.h, p, steps)
+            clocks.start()
+            t = [float(qs.qs_plan_profile(st.h, p, steps).sum()) for _ in range(args.steps)]
+            clk = clocks.stop()
+            launches += steps * args.steps
+            res[tag + "_ms"] = float(np.median(t))
+            res[tag + "_passes"] = qs.qs_plan_info_get(p)["passes"]
+            ms[tag] += res[tag + "_ms"]
+        res["gain"] = res["greedy_ms"] / res["learned_ms"]
+        rows[name] = res
+        qs.qs_plan_destroy(pg)
+        qs.qs_plan_destroy(pl)
+    st.close()
+    qs.qs_model_destroy(model)
+    ngates = sum(len(g) for _, g in circuits)
+    return {
+        "metric": "gates/s", "value": ngates / (ms["learned"] / 1e3), "unit": "gates/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms["learned"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": w["dtype"],
+        "data": "synthetic (seeded layered depth-80 + QFT)",
+        "config": {"workload": args.workload, "qubits": n, "gates": ngates, "planner": "learned",
+                   "l2": "state larger than L2"},
+        "greedy": {"gates_per_s": ngates / (ms["greedy"] / 1e3), "ms_per_step": ms["greedy"]},
+        "gain_vs_greedy": ms["greedy"] / ms["learned"], "circuits": rows, "clocks": clk,
+        "gpu_launches": launches,
     }
 
 # ----------------------------------------------------------------------------- GPU leg
@@ -458,6 +523,10 @@ def main():
         if rank != 0:
             return
         line = run_batch(args, w)
+    elif w["kind"] == "learned":
+        if rank != 0:
+            return
+        line = run_learned(args, w)
     else:
         line = run_gpu(args, w, ws, rank, local)
     if line is None:

@@ -101,7 +101,10 @@ typedef struct {
                             from the state) */
     int32_t stage_bits;  /* register-stage width: slab bits held in registers per thread
                             (complex64: 4 or 5, complex128: 3 or 4; 0 = automatic) */
-    int32_t reserved[4];
+    int32_t fuse_force;  /* 1 = merge dense runs up to fuse_width even where the analytic
+                            cost model says the wider gate costs more (a learned-planner
+                            candidate); 0 = merge only where the model says it pays */
+    int32_t reserved[3];
 } qs_options;
 
 /* Plan summary (qs_plan_info). */
@@ -121,6 +124,17 @@ typedef struct {
     int32_t stage_ops;     /* ops executed inside register stages */
     int32_t smem_ops;      /* ops executed directly on the shared-memory slab */
     int32_t stage_bits;    /* register-stage width */
+    /* learned planner (qs_fuse_learned); zero for greedy plans */
+    int32_t learned;       /* 1 when the plan came from the learned planner */
+    int32_t candidates;    /* candidate plans scored by the cost model */
+    int32_t chosen;        /* index of the chosen candidate, -1 = the greedy plan itself */
+    int32_t judge_state;   /* 0/1: next apply times the learned/greedy plan; 2: settled */
+    double predicted_ms;         /* model's device-time prediction of the chosen plan */
+    double greedy_predicted_ms;  /* ... and of the greedy plan */
+    double judge_ms_learned;     /* measured device time of the first learned apply (0 = none) */
+    double judge_ms_greedy;      /* measured device time of the first greedy apply (0 = none) */
+    int32_t using_greedy;  /* 1 once the judge found the greedy plan faster */
+    int32_t pad_;
 } qs_plan_info;
 
 /* Per-state counters, accumulated since creation or the last qs_stats_reset.  The *_ms fields
@@ -285,6 +299,94 @@ qs_status qs_batch_tune(qs_batch *b, const qs_pauli_term *terms, size_t nterms, 
 
 qs_status qs_batch_info_get(const qs_batch *b, qs_batch_info *out);
 qs_status qs_batch_destroy(qs_batch *b);
+
+/* ------------------------------------------------------------ learned cost model
+ *
+ * Not in the paper, whose planner is the greedy one (Alg. 1-2).  A 3-layer perceptron (FP32,
+ * hidden width 128, ReLU) predicts the device time of one plan step from QS_PLAN_FEATURES
+ * numbers that describe it; its forward, backward and Adam kernels are the library's own.
+ * The learned planner builds a grid of candidate plans (fusion width, forced or cost-checked
+ * fusion, slab bits, register-stage width), scores every step of every candidate in one
+ * batched forward launch, and keeps the candidate with the lowest predicted total.  The greedy
+ * plan (the caller's options as given) is the fallback -- it is kept when no candidate is
+ * predicted faster by more than 2% -- and the judge: a learned plan carries its greedy twin,
+ * the first qs_apply_plan times the learned plan, the second times the greedy plan, and every
+ * later apply uses whichever was faster.  Both compute the same circuit.
+ *
+ * Model target: y = ln(step_ms) - (n - 20) ln 2 (log device time per 2^20 amplitudes).
+ *
+ * Features of one plan step (row of qs_plan_features), in order:
+ *   0 n                         1 dtype (0 = complex64, 1 = complex128)
+ *   2-5 step kind one-hot: slab pass, remap pass, unblocked op, tensor-core gate
+ *   6 slab bits b (unblocked: op width)   7 low segment bits   8 gathered high bits
+ *   9 store permutation (0/1)  10 lowest gathered position  11 highest gathered position
+ *  12 register-stage width     13 ops in the pass           14 register stages
+ *  15 stage sub-ops   16 1-qubit complex   17 1-qubit real   18 2-qubit   19 phases
+ *  20 diagonal tables   21 X / SWAP relabels   22 shared-memory dense ops
+ *  23 sum of 2^k over shared-memory dense ops   24 other shared-memory ops
+ *  25 ops with controls   26 analytic real FMAs per amplitude   27 widest dense op */
+#define QS_PLAN_FEATURES 28
+
+typedef struct qs_model qs_model;
+
+typedef struct {
+    int32_t nfeat, hidden, nparams;
+    int32_t steps;       /* Adam steps taken */
+    float ym, ys;        /* target standardisation */
+    float last_loss;     /* mean squared error (standardised) of the last training epoch */
+    int32_t pad_;
+} qs_model_info;
+
+typedef struct {
+    int32_t epochs;      /* passes over the data */
+    int32_t batch;       /* rows per Adam step (multiple of 32 recommended) */
+    float lr;            /* Adam step size */
+    int32_t fit_norm;    /* 1 = set feature / target standardisation from this data first */
+    uint64_t seed;       /* row shuffle (fixed for all epochs) */
+    int32_t graph;       /* 1 = replay each epoch from a captured CUDA graph */
+    int32_t reserved[3];
+} qs_train_options;
+
+void qs_train_options_default(qs_train_options *o);
+
+/* New model with nfeat inputs (<= 32), He-uniform weights from a SplitMix64 stream seeded
+ * with `seed`, zero biases, identity standardisation, on the current device. */
+qs_status qs_model_create(int nfeat, uint64_t seed, qs_model **out);
+qs_status qs_model_destroy(qs_model *m);
+qs_status qs_model_info_get(const qs_model *m, qs_model_info *out);
+/* Flat FP32 parameters [W1 (nfeat x 128) | b1 | W2 (128 x 128) | b2 | W3 (128) | b3], row-major,
+ * input index first.  count must equal nparams.  set resets the Adam moments and step. */
+qs_status qs_model_get_params(const qs_model *m, float *host, size_t count);
+qs_status qs_model_set_params(qs_model *m, const float *host, size_t count);
+/* Standardisation: inputs x' = (x - mu) / sd per feature, targets t' = (t - ym) / ys. */
+qs_status qs_model_get_norm(const qs_model *m, float *mu, float *sd, float *ym, float *ys);
+qs_status qs_model_set_norm(qs_model *m, const float *mu, const float *sd, float ym, float ys);
+/* y[r] = model(X[r]) for host row-major X (rows x nfeat); predictions de-standardised. */
+qs_status qs_model_predict(qs_model *m, const float *X, size_t rows, float *y);
+/* Gradient of the mean squared error (standardised space) over the rows; grad has nparams
+ * entries; *loss receives the error.  No update. */
+qs_status qs_model_loss_grad(qs_model *m, const float *X, const float *T, size_t rows, float *grad,
+                             float *loss);
+/* Adam training on the device: rows are shuffled once, split into batches of o->batch rows
+ * (the remainder is dropped when rows > batch), and each epoch takes one step per batch.
+ * *final_loss (may be NULL) receives the mean batch loss of the last epoch. */
+qs_status qs_model_train(qs_model *m, const float *X, const float *T, size_t rows,
+                         const qs_train_options *o, float *final_loss);
+
+/* Features of every step of a plan (rows x QS_PLAN_FEATURES, host, row-major).  *nrows receives
+ * the step count; QS_EINVAL if cap_rows is smaller. */
+qs_status qs_plan_features(const qs_plan *p, float *out, size_t cap_rows, size_t *nrows);
+/* Apply a plan like qs_apply_plan and write each step's device time (ms, CUDA events on the
+ * state's stream) to step_ms[0..steps).  Synchronises. */
+qs_status qs_plan_profile(qs_state *s, const qs_plan *p, float *step_ms, size_t cap);
+/* Learned planner: as qs_fuse, then choose among candidate plans with the model (see above).
+ * With model NULL, or options that fix the plan (blocking off, tensor cores on), it returns
+ * the greedy plan. */
+qs_status qs_fuse_learned(const qs_gate *gates, size_t ngates, int n, const qs_options *o,
+                          qs_model *model, qs_plan **out);
+/* Process-wide model used when options.planner = QS_PLANNER_LEARNED in qs_fuse and
+ * qs_apply_circuit (NULL = none: those calls plan greedily).  The caller keeps ownership. */
+qs_status qs_set_cost_model(qs_model *m);
 
 /* ------------------------------------------------------------------------- misc */
 

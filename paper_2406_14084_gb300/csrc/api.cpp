@@ -15,6 +15,8 @@
 #include <string>
 #include <vector>
 
+#include "learned.h"
+#include "model.h"
 #include "planner.h"
 #include "qs_internal.h"
 
@@ -131,6 +133,14 @@ struct qs_state {
 struct qs_plan {
     Plan p;
     DevPlanBuf dev[2];  // per dtype
+    // learned planner: the greedy twin (judge), predictions, and the judge's measurements
+    std::unique_ptr<qs_plan> alt;
+    bool learned = false;
+    int candidates = 0, chosen = -1;
+    double pred_ms = 0, greedy_pred_ms = 0;
+    int judge_state = 2;       // 0: next apply times this plan, 1: times alt, 2: settled
+    double judge_ms[2] = {0, 0};
+    bool use_alt = false;
     ~qs_plan()
     {
         for (auto &d : dev)
@@ -238,7 +248,29 @@ qs_status check_device(qs_state *s)
     return QS_OK;
 }
 
-qs_status run_plan(qs_state *s, qs_plan *pl)
+// Per-launch event pairs for qs_plan_profile and the learned planner's judge.
+struct StepTimer {
+    std::vector<cudaEvent_t> ev;  // ev[i] recorded before step i; ev.back() after the last
+    ~StepTimer()
+    {
+        for (cudaEvent_t e : ev) cudaEventDestroy(e);
+    }
+    void mark(cudaStream_t s)
+    {
+        cudaEvent_t e = nullptr;
+        cudaEventCreate(&e);
+        cudaEventRecord(e, s);
+        ev.push_back(e);
+    }
+    float between(size_t i, size_t j) const
+    {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, ev[i], ev[j]);
+        return ms;
+    }
+};
+
+qs_status run_plan(qs_state *s, qs_plan *pl, StepTimer *timer = nullptr)
 {
     if (fault("launch")) return fail(QS_ECUDA, "injected launch failure");
     qs_status st = upload(pl, s->dt);
@@ -248,6 +280,7 @@ qs_status run_plan(qs_state *s, qs_plan *pl)
     LaunchCtx c{s->amp, s->n, s->dt, (void *)s->stream};
     char err[256] = {0};
     const int64_t pass_bytes = int64_t(2) * (int64_t(1) << s->n) * (int64_t)amp_bytes(s->dt);
+    if (timer) timer->mark(s->stream);
     for (const Step &stp : p.steps) {
         int rc = QS_OK;
         cudaEvent_t ev0 = nullptr;
@@ -286,6 +319,7 @@ qs_status run_plan(qs_state *s, qs_plan *pl)
             if (s->pending.size() > 4096) s->fold_timings();
         }
         if (rc) return fail((qs_status)rc, err);
+        if (timer) timer->mark(s->stream);
     }
     s->stats.plans_applied++;
     return QS_OK;
@@ -303,6 +337,34 @@ qs_status canonicalize_state(qs_state *s)
     // plan buffers are freed by the destructor; wait so the free cannot race the kernels
     cudaStreamSynchronize(s->stream);
     for (int q = 0; q < s->n; ++q) s->phys_of[q] = q;
+    return QS_OK;
+}
+
+// Learned planner: greedy plan plus, when the model predicts a faster candidate, that
+// candidate with the greedy plan attached as its judge.
+qs_status fuse_learned(const std::vector<CGate> &cg, int n, const qs_options &opt, qs_model *model, qs_plan **out)
+{
+    std::unique_ptr<qs_plan> greedy(new qs_plan()), best(new qs_plan());
+    LearnedMeta meta;
+    std::string err;
+    qs_options gopt = opt;
+    gopt.planner = QS_PLANNER_GREEDY;
+    int rc = learned_choose(cg, n, (qs_dtype)opt.dtype, gopt, model, greedy->p, best->p, meta, err);
+    if (rc) return fail((qs_status)rc, err);
+    qs_plan *res;
+    if (meta.chosen >= 0) {
+        best->alt = std::move(greedy);
+        best->judge_state = 0;
+        res = best.release();
+    } else {
+        res = greedy.release();
+    }
+    res->learned = model != nullptr;
+    res->candidates = meta.candidates;
+    res->chosen = meta.chosen;
+    res->pred_ms = meta.predicted_ms;
+    res->greedy_pred_ms = meta.greedy_ms;
+    *out = res;
     return QS_OK;
 }
 
@@ -505,6 +567,7 @@ qs_status qs_fuse(const qs_gate *g, size_t ng, int n, const qs_options *o, qs_pl
     int rc = canonicalize(g, ng, n, cg, err);
     if (rc) return fail((qs_status)rc, err);
     if (opt.dtype != QS_C64 && opt.dtype != QS_C128) return fail(QS_EINVAL, "bad options dtype");
+    if (opt.planner == QS_PLANNER_LEARNED) return fuse_learned(cg, n, opt, default_cost_model(), out);
     std::unique_ptr<qs_plan> pl(new qs_plan());
     // A plan can be applied to either precision; opt.dtype selects the cost model it is
     // optimised for (and the slab size, which must fit shared memory at apply time).
@@ -512,6 +575,29 @@ qs_status qs_fuse(const qs_gate *g, size_t ng, int n, const qs_options *o, qs_pl
     if (rc) return fail((qs_status)rc, err);
     *out = pl.release();
     return QS_OK;
+    QS_GUARD_END
+}
+
+qs_status qs_fuse_learned(const qs_gate *g, size_t ng, int n, const qs_options *o, qs_model *model, qs_plan **out)
+{
+    QS_GUARD_BEGIN
+    g_err.clear();
+    if (!out) return fail(QS_EINVAL, "out is NULL");
+    if (!g && ng) return fail(QS_EINVAL, "gates is NULL");
+    if (n < 1 || n > QS_MAX_QUBITS) return fail(QS_EINVAL, "n must be in [1, 36]");
+    qs_options opt;
+    if (o) opt = *o;
+    else qs_options_default(&opt);
+    if (opt.fuse_width < 0 || opt.fuse_width > 7 || opt.slab_bits < 0 || opt.slab_bits > kMaxSlabBits ||
+        opt.seg_bits < 0 || opt.seg_bits > 8 || (opt.slab_mode != QS_SLAB_GATHER && opt.slab_mode != QS_SLAB_REMAP) ||
+        (opt.tc != QS_TC_OFF && opt.tc != QS_TC_TF32X3 && opt.tc != QS_TC_BF16X3) ||
+        (opt.dtype != QS_C64 && opt.dtype != QS_C128))
+        return fail(QS_EINVAL, "option out of range");
+    std::vector<CGate> cg;
+    std::string err;
+    int rc = canonicalize(g, ng, n, cg, err);
+    if (rc) return fail((qs_status)rc, err);
+    return fuse_learned(cg, n, opt, model, out);
     QS_GUARD_END
 }
 
@@ -555,6 +641,15 @@ qs_status qs_plan_info_get(const qs_plan *p, qs_plan_info *out)
                 if (p->p.ops[o].type != OP_STAGE) out->smem_ops++;
         }
     out->stage_bits = p->p.stage_bits;
+    out->learned = p->learned ? 1 : 0;
+    out->candidates = p->candidates;
+    out->chosen = p->chosen;
+    out->judge_state = p->judge_state;
+    out->predicted_ms = p->pred_ms;
+    out->greedy_predicted_ms = p->greedy_pred_ms;
+    out->judge_ms_learned = p->judge_ms[0];
+    out->judge_ms_greedy = p->judge_ms[1];
+    out->using_greedy = (p->alt && p->use_alt) ? 1 : 0;
     return QS_OK;
 }
 
@@ -731,9 +826,61 @@ qs_status qs_apply_plan(qs_state *s, const qs_plan *p)
         if (ps.b > bmax) return fail(QS_EINVAL, "plan slab too large for this dtype");
     qs_status st = canonicalize_state(s);
     if (st) return st;
-    st = run_plan(s, const_cast<qs_plan *>(p));
+    qs_plan *pl = const_cast<qs_plan *>(p);
+    if (pl->alt && pl->judge_state < 2) {
+        // the judge: time this plan on its first apply and the greedy twin on the second
+        qs_plan *run = pl->judge_state == 0 ? pl : pl->alt.get();
+        StepTimer timer;
+        st = run_plan(s, run, &timer);
+        if (st) return st;
+        st = cuda_status(cudaEventSynchronize(timer.ev.back()), "judge timing");
+        if (st) return st;
+        pl->judge_ms[pl->judge_state] = timer.between(0, timer.ev.size() - 1);
+        if (++pl->judge_state == 2) pl->use_alt = pl->judge_ms[1] < pl->judge_ms[0];
+        s->phys_of = run->p.final_phys_of;
+        return QS_OK;
+    }
+    qs_plan *run = (pl->alt && pl->use_alt) ? pl->alt.get() : pl;
+    st = run_plan(s, run);
     if (st) return st;
+    s->phys_of = run->p.final_phys_of;
+    return QS_OK;
+    QS_GUARD_END
+}
+
+qs_status qs_plan_profile(qs_state *s, const qs_plan *p, float *step_ms, size_t cap)
+{
+    QS_GUARD_BEGIN
+    if (!s || !p || (!step_ms && cap)) return fail(QS_EINVAL, "NULL argument");
+    if (p->p.n != s->n) return fail(QS_EINVAL, "plan and state have different qubit counts");
+    if (p->p.dt != s->dt) return fail(QS_EINVAL, "plan was built for the other precision (options.dtype)");
+    if (cap < p->p.steps.size()) return fail(QS_EINVAL, "step_ms has fewer entries than the plan has steps");
+    const int bmax = max_slab_bits(s->dt);
+    for (const DevPass &ps : p->p.passes)
+        if (ps.b > bmax) return fail(QS_EINVAL, "plan slab too large for this dtype");
+    qs_status st = canonicalize_state(s);
+    if (st) return st;
+    StepTimer timer;
+    st = run_plan(s, const_cast<qs_plan *>(p), &timer);
+    if (st) return st;
+    st = cuda_status(cudaEventSynchronize(timer.ev.back()), "step timing");
+    if (st) return st;
+    for (size_t i = 0; i + 1 < timer.ev.size(); ++i) step_ms[i] = timer.between(i, i + 1);
     s->phys_of = p->p.final_phys_of;
+    return check_device(s);
+    QS_GUARD_END
+}
+
+qs_status qs_plan_features(const qs_plan *p, float *out, size_t cap_rows, size_t *nrows)
+{
+    QS_GUARD_BEGIN
+    if (!p || !nrows || (!out && cap_rows)) return fail(QS_EINVAL, "NULL argument");
+    std::vector<float> rows;
+    plan_features(p->p, rows);
+    const size_t r = rows.size() / QS_PLAN_FEATURES;
+    *nrows = r;
+    if (cap_rows < r) return fail(QS_EINVAL, "output has fewer rows than the plan has steps");
+    if (r) std::memcpy(out, rows.data(), rows.size() * sizeof(float));
     return QS_OK;
     QS_GUARD_END
 }

@@ -1045,7 +1045,7 @@ int build_plan(const std::vector<CGate> &gates_in, int n, qs_dtype dt, const qs_
         int kdense = std::min(opt.fuse_width, kMaxDense);
         if (opt.blocking) kdense = std::min(kdense, lowblock ? b : std::max(1, b - lo));
         gates = fuse_pass(gates, kdiag, 0, false, true, dt);
-        gates = fuse_pass(gates, kdiag, kdense, false, false, dt);
+        gates = fuse_pass(gates, kdiag, kdense, opt.fuse_force != 0, false, dt);
     }
     if (is_tc.empty()) is_tc.assign(gates.size(), 0);
     for (size_t gi = 0; gi < gates.size(); ++gi) {

@@ -77,6 +77,9 @@ int plan_remap(int n, qs_dtype dt, const std::vector<int> &A, const std::vector<
 // Analytic per-amplitude cost of one op, in FP32-FMA-equivalents (greedy planner's model).
 double op_cost(const CGate &g, qs_dtype dt);
 
+// Append one row of QS_PLAN_FEATURES numbers per plan step (learned.cpp).
+void plan_features(const Plan &p, std::vector<float> &rows);
+
 // Default slab and segment bits for a dtype.
 int default_slab_bits(qs_dtype dt);
 int default_seg_bits(qs_dtype dt);

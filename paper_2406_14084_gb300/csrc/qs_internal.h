@@ -205,4 +205,29 @@ constexpr int kStaticProbsMaxQubits = 14;
 int launch_probs_static(const LaunchCtx &c, const int *phys_q, int nq, double *h_out, char *err,
                         size_t errlen);
 
+// Cost-model network (k_mlp.cu): 3-layer perceptron, FP32, hidden width kMlpHidden.
+constexpr int kMlpHidden = 128;
+constexpr int kMlpMaxFeatures = 32;
+struct MlpArgs {
+    const float *X;       // B x F inputs (raw; standardised on load)
+    const float *T;       // B targets (raw; standardised on use), training only
+    int B, F;
+    float *params;        // flat [W1 | b1 | W2 | b2 | W3 | b3]
+    const float *mu;      // F feature means
+    const float *inv_sd;  // F reciprocal feature spreads
+    float ym, ys, inv_ys; // target mean, spread, 1/spread
+    float scale;          // training: 2 / B (derivative of the mean squared error)
+    float *y_out;         // forward: B predictions (de-standardised)
+    float *partial;       // training: tiles x pstride partial gradients
+    int pstride, nparams;
+    int *step_counter;    // Adam step t (advanced once per training step), or NULL
+    float *grad_out;      // gradient output when not updating
+    float *loss_out;      // mean squared error (standardised space) of the batch
+    float *adam_m, *adam_v;
+};
+int mlp_param_count(int F);
+int mlp_tiles(int B);
+int launch_mlp_forward(const MlpArgs &a, void *stream, char *err, size_t errlen);
+int launch_mlp_train_step(const MlpArgs &a, int update, float lr, void *stream, char *err, size_t errlen);
+
 }  // namespace qs

@@ -53,7 +53,8 @@ class QsOptions(ctypes.Structure):
                 ("slab_mode", ctypes.c_int32), ("planner", ctypes.c_int32), ("tc", ctypes.c_int32),
                 ("tc_width", ctypes.c_int32), ("graph", ctypes.c_int32),
                 ("diag_bits", ctypes.c_int32), ("dtype", ctypes.c_int32),
-                ("stage_bits", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
+                ("stage_bits", ctypes.c_int32), ("fuse_force", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 3)]
 
 
 class QsPlanInfo(ctypes.Structure):
@@ -63,7 +64,27 @@ class QsPlanInfo(ctypes.Structure):
                 ("seg_bits", ctypes.c_int32), ("flops_per_amp", ctypes.c_double),
                 ("device_bytes", ctypes.c_int64), ("stages", ctypes.c_int32),
                 ("stage_ops", ctypes.c_int32), ("smem_ops", ctypes.c_int32),
-                ("stage_bits", ctypes.c_int32)]
+                ("stage_bits", ctypes.c_int32), ("learned", ctypes.c_int32),
+                ("candidates", ctypes.c_int32), ("chosen", ctypes.c_int32),
+                ("judge_state", ctypes.c_int32), ("predicted_ms", ctypes.c_double),
+                ("greedy_predicted_ms", ctypes.c_double), ("judge_ms_learned", ctypes.c_double),
+                ("judge_ms_greedy", ctypes.c_double), ("using_greedy", ctypes.c_int32),
+                ("pad_", ctypes.c_int32)]
+
+
+QS_PLAN_FEATURES = 28
+
+
+class QsModelInfo(ctypes.Structure):
+    _fields_ = [("nfeat", ctypes.c_int32), ("hidden", ctypes.c_int32), ("nparams", ctypes.c_int32),
+                ("steps", ctypes.c_int32), ("ym", ctypes.c_float), ("ys", ctypes.c_float),
+                ("last_loss", ctypes.c_float), ("pad_", ctypes.c_int32)]
+
+
+class QsTrainOptions(ctypes.Structure):
+    _fields_ = [("epochs", ctypes.c_int32), ("batch", ctypes.c_int32), ("lr", ctypes.c_float),
+                ("fit_norm", ctypes.c_int32), ("seed", ctypes.c_uint64), ("graph", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 3)]
 
 
 class QsBatchInfo(ctypes.Structure):
@@ -85,6 +106,7 @@ _vp = ctypes.c_void_p
 _i = ctypes.c_int
 _u64 = ctypes.c_uint64
 _dp = ctypes.POINTER(ctypes.c_double)
+_fp = ctypes.POINTER(ctypes.c_float)
 
 # name -> (argtypes); restype is qs_status (int) unless listed in _RESTYPE
 _SIGS = {
@@ -119,10 +141,27 @@ _SIGS = {
     "qs_batch_tune": [_vp, ctypes.POINTER(QsPauliTerm), ctypes.c_size_t, ctypes.POINTER(_i)],
     "qs_batch_info_get": [_vp, ctypes.POINTER(QsBatchInfo)],
     "qs_batch_destroy": [_vp],
+    "qs_train_options_default": [ctypes.POINTER(QsTrainOptions)],
+    "qs_model_create": [_i, _u64, ctypes.POINTER(_vp)],
+    "qs_model_destroy": [_vp],
+    "qs_model_info_get": [_vp, ctypes.POINTER(QsModelInfo)],
+    "qs_model_get_params": [_vp, _fp, ctypes.c_size_t],
+    "qs_model_set_params": [_vp, _fp, ctypes.c_size_t],
+    "qs_model_get_norm": [_vp, _fp, _fp, _fp, _fp],
+    "qs_model_set_norm": [_vp, _fp, _fp, ctypes.c_float, ctypes.c_float],
+    "qs_model_predict": [_vp, _fp, ctypes.c_size_t, _fp],
+    "qs_model_loss_grad": [_vp, _fp, _fp, ctypes.c_size_t, _fp, _fp],
+    "qs_model_train": [_vp, _fp, _fp, ctypes.c_size_t, ctypes.POINTER(QsTrainOptions), _fp],
+    "qs_plan_features": [_vp, _fp, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)],
+    "qs_plan_profile": [_vp, _vp, _fp, ctypes.c_size_t],
+    "qs_fuse_learned": [ctypes.POINTER(QsGate), ctypes.c_size_t, _i, ctypes.POINTER(QsOptions), _vp,
+                        ctypes.POINTER(_vp)],
+    "qs_set_cost_model": [_vp],
     "qs_last_error": [],
     "qs_version": [],
 }
-_RESTYPE = {"qs_last_error": ctypes.c_char_p, "qs_version": ctypes.c_char_p, "qs_options_default": None}
+_RESTYPE = {"qs_last_error": ctypes.c_char_p, "qs_version": ctypes.c_char_p, "qs_options_default": None,
+            "qs_train_options_default": None}
 
 
 def library_path() -> str:
@@ -273,6 +312,117 @@ def qs_fuse(gates, n: int, opts: QsOptions | None = None):
 
 def qs_plan_destroy(plan):
     _check(lib().qs_plan_destroy(plan))
+
+
+def qs_fuse_learned(gates, n: int, opts: QsOptions | None, model):
+    arr, keep = marshal_gates(gates)
+    h = _vp()
+    _check(lib().qs_fuse_learned(arr, len(gates), n, ctypes.byref(opts) if opts is not None else None,
+                                 model, ctypes.byref(h)))
+    return h
+
+
+def qs_plan_features(plan) -> np.ndarray:
+    """Per-step feature rows of a plan, shape (steps, QS_PLAN_FEATURES), float32."""
+    nrows = ctypes.c_size_t()
+    rc = lib().qs_plan_features(plan, None, 0, ctypes.byref(nrows))  # size query
+    if rc not in (QS_OK, QS_EINVAL):
+        _check(rc)
+    out = np.zeros((nrows.value, QS_PLAN_FEATURES), dtype=np.float32)
+    _check(lib().qs_plan_features(plan, _f32(out), nrows.value, ctypes.byref(nrows)))
+    return out
+
+
+def qs_plan_profile(state, plan, steps: int) -> np.ndarray:
+    """Apply a plan, returning each step's device time in ms."""
+    out = np.zeros(max(1, steps), dtype=np.float32)
+    _check(lib().qs_plan_profile(state, plan, _f32(out), out.size))
+    return out[:steps]
+
+
+def _f32(a: np.ndarray):
+    assert a.dtype == np.float32 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(_fp)
+
+
+def qs_train_options(**kw) -> QsTrainOptions:
+    o = QsTrainOptions()
+    lib().qs_train_options_default(ctypes.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise AttributeError(k)
+        setattr(o, k, v)
+    return o
+
+
+def qs_model_create(nfeat: int = QS_PLAN_FEATURES, seed: int = 1):
+    h = _vp()
+    _check(lib().qs_model_create(nfeat, seed, ctypes.byref(h)))
+    return h
+
+
+def qs_model_destroy(model):
+    _check(lib().qs_model_destroy(model))
+
+
+def qs_model_info_get(model) -> dict:
+    info = QsModelInfo()
+    _check(lib().qs_model_info_get(model, ctypes.byref(info)))
+    return {f: getattr(info, f) for f, _ in QsModelInfo._fields_}
+
+
+def qs_model_get_params(model) -> np.ndarray:
+    out = np.zeros(qs_model_info_get(model)["nparams"], dtype=np.float32)
+    _check(lib().qs_model_get_params(model, _f32(out), out.size))
+    return out
+
+
+def qs_model_set_params(model, params):
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    _check(lib().qs_model_set_params(model, _f32(p), p.size))
+
+
+def qs_model_get_norm(model):
+    F = qs_model_info_get(model)["nfeat"]
+    mu, sd = np.zeros(F, dtype=np.float32), np.zeros(F, dtype=np.float32)
+    ym, ys = ctypes.c_float(), ctypes.c_float()
+    _check(lib().qs_model_get_norm(model, _f32(mu), _f32(sd), ctypes.byref(ym), ctypes.byref(ys)))
+    return mu, sd, ym.value, ys.value
+
+
+def qs_model_set_norm(model, mu, sd, ym: float, ys: float):
+    mu = np.ascontiguousarray(mu, dtype=np.float32)
+    sd = np.ascontiguousarray(sd, dtype=np.float32)
+    _check(lib().qs_model_set_norm(model, _f32(mu), _f32(sd), float(ym), float(ys)))
+
+
+def qs_model_predict(model, X) -> np.ndarray:
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    y = np.zeros(X.shape[0], dtype=np.float32)
+    _check(lib().qs_model_predict(model, _f32(X), X.shape[0], _f32(y)))
+    return y
+
+
+def qs_model_loss_grad(model, X, T):
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    T = np.ascontiguousarray(T, dtype=np.float32)
+    g = np.zeros(qs_model_info_get(model)["nparams"], dtype=np.float32)
+    loss = ctypes.c_float()
+    _check(lib().qs_model_loss_grad(model, _f32(X), _f32(T), X.shape[0], _f32(g), ctypes.byref(loss)))
+    return loss.value, g
+
+
+def qs_model_train(model, X, T, opts: QsTrainOptions | None = None) -> float:
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    T = np.ascontiguousarray(T, dtype=np.float32)
+    loss = ctypes.c_float()
+    _check(lib().qs_model_train(model, _f32(X), _f32(T), X.shape[0],
+                                ctypes.byref(opts) if opts is not None else None, ctypes.byref(loss)))
+    return loss.value
+
+
+def qs_set_cost_model(model):
+    _check(lib().qs_set_cost_model(model))
 
 
 def qs_plan_info_get(plan) -> dict:

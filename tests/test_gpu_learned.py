@@ -1,0 +1,132 @@
+"""Learned planner on the device: identical results, the greedy judge, and the gain.
+
+The shipped model (paper_2406_14084_gb300/data/cost_model.npz) was trained by
+``python -m paper_2406_14084_gb300.costmodel`` on step timings this library measured on a
+GB300.  Every plan the learned planner returns computes the same circuit as the greedy plan,
+so outputs are checked against the FP64 oracle at the complex128 tolerance (1e-12)."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2406_14084_gb300 import costmodel
+from paper_2406_14084_gb300 import qs
+from paper_2406_14084_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+MODEL = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_2406_14084_gb300",
+                     "data", "cost_model.npz")
+
+
+@pytest.fixture(scope="module")
+def model():
+    m = costmodel.load(MODEL)
+    yield m
+    qs.qs_model_destroy(m)
+
+
+def run(n, dtype, gates, plan, times=1):
+    outs = []
+    with qs.State(n, dtype) as st:
+        for _ in range(times):
+            qs.qs_set_basis(st.h, 0)
+            qs.qs_apply_plan(st.h, plan)
+            outs.append(st.amplitudes())
+    return outs
+
+
+@pytest.mark.parametrize("name", ["qft", "layered", "random"])
+def test_learned_plans_match_oracle_through_the_judge(model, name):
+    n = 20
+    gates = {"qft": W.qft(n), "layered": W.layered(n, 6, 31), "random": W.random_circuit(n, 150, 32)}[name]
+    want = oracle.apply_circuit(n, gates)
+    for dtype, tol in ((qs.QS_C128, 1e-12), (qs.QS_C64, 1e-5)):
+        p = qs.qs_fuse_learned(gates, n, qs.options(dtype=dtype), model)
+        try:
+            info = qs.qs_plan_info_get(p)
+            assert info["learned"] == 1 and info["candidates"] >= 2
+            # apply three times: learned (timed), greedy twin (timed), then the faster one
+            for a in run(n, dtype, gates, p, times=3):
+                assert np.max(np.abs(a - want)) <= tol
+            info = qs.qs_plan_info_get(p)
+            if info["chosen"] >= 0:
+                assert info["judge_state"] == 2
+                assert info["judge_ms_learned"] > 0 and info["judge_ms_greedy"] > 0
+                assert info["using_greedy"] == int(info["judge_ms_greedy"] < info["judge_ms_learned"])
+            else:
+                assert info["judge_state"] == 2 and info["using_greedy"] == 0
+        finally:
+            qs.qs_plan_destroy(p)
+
+
+def test_planner_option_uses_the_registered_model(model):
+    n = 18
+    gates = W.qft(n)
+    qs.qs_set_cost_model(model)
+    try:
+        p = qs.qs_fuse(gates, n, qs.options(dtype=qs.QS_C128, planner=qs.QS_PLANNER_LEARNED))
+        assert qs.qs_plan_info_get(p)["learned"] == 1
+        qs.qs_plan_destroy(p)
+        with qs.State(n, qs.QS_C128) as st:
+            st.apply(gates, qs.options(dtype=qs.QS_C128, planner=qs.QS_PLANNER_LEARNED))
+            assert np.max(np.abs(st.amplitudes() - oracle.apply_circuit(n, gates))) <= 1e-12
+    finally:
+        qs.qs_set_cost_model(None)
+
+
+def test_profile_reports_every_step():
+    n = 24
+    gates = W.layered(n, 4, 5)
+    p = qs.qs_fuse(gates, n, qs.options(dtype=qs.QS_C64))
+    try:
+        steps = qs.qs_plan_features(p).shape[0]
+        with qs.State(n, qs.QS_C64) as st:
+            ms = qs.qs_plan_profile(st.h, p, steps)
+            assert ms.shape == (steps,) and np.all(ms > 0)
+            with pytest.raises(qs.QsError):
+                qs.qs_plan_profile(st.h, p, steps - 1)
+    finally:
+        qs.qs_plan_destroy(p)
+
+
+def test_collect_and_train_small():
+    X, y, meta = costmodel.collect(300, seed=5, nmin=20, nmax=21, repeats=1, time_budget_s=60)
+    assert X.shape[0] >= 100 and X.shape[1] == qs.QS_PLAN_FEATURES and np.all(np.isfinite(y))
+    m, loss = costmodel.train(X, y, epochs=40)
+    try:
+        pred = qs.qs_model_predict(m, X)
+        assert np.all(np.isfinite(pred))
+        assert np.sqrt(np.mean((pred - y) ** 2)) < np.std(y)  # better than the mean predictor
+    finally:
+        qs.qs_model_destroy(m)
+
+
+def plan_ms(st, plan, reps=3):
+    steps = qs.qs_plan_features(plan).shape[0]
+    return min(float(qs.qs_plan_profile(st.h, plan, steps).sum()) for _ in range(reps))
+
+
+def test_learned_planner_gain_over_greedy(model, capsys):
+    """What the trained network buys: device time of the greedy plan and of the learned pick on
+    the same state, best of 3.  The learned pick may never be slower than greedy (2% timing
+    slack), and it must win clearly on at least one of the circuit families."""
+    cases = [("qft", 28, qs.QS_C128, W.qft(28)), ("random", 28, qs.QS_C128, W.random_circuit(28, 300, 79)),
+             ("layered", 29, qs.QS_C64, W.layered(29, 16, 78))]
+    gains = []
+    for name, n, dtype, gates in cases:
+        g = qs.qs_fuse(gates, n, qs.options(dtype=dtype))
+        l = qs.qs_fuse_learned(gates, n, qs.options(dtype=dtype), model)
+        try:
+            with qs.State(n, dtype) as st:
+                tg, tl = plan_ms(st, g), plan_ms(st, l)
+        finally:
+            qs.qs_plan_destroy(g)
+            qs.qs_plan_destroy(l)
+        gains.append(tg / tl)
+        with capsys.disabled():
+            print(f"\n  learned planner {name}{n} {'c64' if dtype == 0 else 'c128'}: greedy {tg:.1f} ms, "
+                  f"learned {tl:.1f} ms, gain x{tg / tl:.3f}")
+        assert tl <= 1.02 * tg
+    assert max(gains) >= 1.05
