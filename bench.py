@@ -39,6 +39,7 @@ WORKLOADS = {
     "layered32_c128": dict(n=32, dtype="c128", kind="layered", depth=40, seed=1002),
     "qft32_c128": dict(n=32, dtype="c128", kind="qft", seed=1002),
     "layered30_c64": dict(n=30, dtype="c64", kind="layered", depth=40, seed=1002),
+    "layered28_c64": dict(n=28, dtype="c64", kind="layered", depth=40, seed=1002),
     "precision33_c64": dict(n=33, dtype="c64", kind="layered", depth=60, seed=1003, tc=True),
     "precision30_c64": dict(n=30, dtype="c64", kind="layered", depth=60, seed=1003, tc=True),
     "config1": dict(n=20, dtype="c128", kind="random", ngates=200, seed=1001),
@@ -58,6 +59,36 @@ def make_circuit(w, n=None):
     if w["kind"] == "qft":
         return W.qft(n), W.random_basis(n, w["seed"])
     return W.random_circuit(n, w["ngates"], w["seed"]), 0
+
+
+# Non-tensor ALU peaks from unit counts and the maximum SM clock: 152 SMs x 2.07 GHz x FMA lanes
+# per SM per clock (128 FP32, 2 FP64) x 2 flops per FMA.
+ALU_PEAK_TFLOPS = {"c64": 152 * 2.07e9 * 128 * 2 / 1e12, "c128": 152 * 2.07e9 * 2 * 2 / 1e12}
+
+TRAFFIC_SOURCES = ("k_slab.cu", "slab_common.cuh", "dev_common.cuh", "qs_internal.h")
+
+
+def slab_kernel_hash() -> str:
+    import hashlib
+
+    h = hashlib.sha256()
+    for f in TRAFFIC_SOURCES:
+        with open(os.path.join(ROOT, "paper_2406_14084_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(n: int, dtype: str):
+    """DRAM bytes per slab-pass launch from the committed ncu summary, scaled by 2^(n - n_capture)
+    (every pass streams the whole state once); None if the kernel sources changed since."""
+    p = os.path.join(ROOT, "profiles", "slab_pass_traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        t = json.load(f)
+    if t.get("source_hash") != slab_kernel_hash() or t.get("dtype") != dtype:
+        return None
+    return t["dram_bytes_per_launch"] * 2.0 ** (n - t["n"])
 
 
 def measured_peaks():
@@ -416,6 +447,12 @@ def run_gpu(args, w, ws, rank, local):
     dom_ms = (st["pass_ms"] + st["remap_ms"] + st["unblocked_ms"]) / max(1, npass_timed)
     peaks = measured_peaks()
     achieved = pass_bytes / (dom_ms / 1e3) / 1e9
+    # arithmetic side: algorithmic flops of the plan (8 * 2^k per amplitude for a dense k-qubit
+    # op, 6 for a diagonal) over the summed pass time, against the FP32 / FP64 ALU peak
+    pass_ms_total = st["pass_ms"] + st["remap_ms"] + st["unblocked_ms"]
+    alu_tflops = info["flops_per_amp"] * (1 << n) * args.steps / (pass_ms_total / 1e3) / 1e12
+    alu_peak = ALU_PEAK_TFLOPS["c64" if dtype == qs.QS_C64 else "c128"]
+    traffic = measured_traffic(n, w["dtype"])
     norm = qs.qs_norm2(state.h)
     fidelity = None if args.no_fidelity else fidelity_check(w, opts, dtype)
 
@@ -466,9 +503,13 @@ def run_gpu(args, w, ws, rank, local):
         "fidelity": fidelity,
         "tc": bool(opts.tc),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                     "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                     "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
                      "kernel": "slab_pass_kernel", "peak_source": peaks["source"],
                      "avg_launch_ms": dom_ms, "bytes_per_launch": pass_bytes},
+        "roofline_alu": {"bound": "alu", "achieved": alu_tflops, "peak": alu_peak, "unit": "TFLOP/s",
+                         "frac": alu_tflops / alu_peak, "kernel": "slab_pass_kernel",
+                         "flops_per_amp": info["flops_per_amp"],
+                         "peak_source": "152 SMs x 2.07 GHz x (128 FP32 | 2 FP64) FMA/clk x 2"},
         "clocks": clk,
         "gpu_launches": args.steps * nsteps,
         "e2e": e2e,
