@@ -78,6 +78,27 @@ def slab_kernel_hash() -> str:
     return h.hexdigest()[:16]
 
 
+def circuit_flops_per_amp(gates) -> float:
+    """Algorithmic flops per amplitude of the unfused circuit: a dense k-qubit gate is a 2^k x 2^k
+    complex matrix-vector product (8 * 2^k flops per amplitude, over the 2^-c of amplitudes its c
+    controls select); a diagonal costs 6 flops on the amplitudes it changes; X / CX / SWAP none."""
+    f = 0.0
+    for g in gates:
+        k, c = len(g.targets), len(g.controls)
+        sel = 2.0 ** -c
+        if g.kind in ("X", "CX", "SWAP"):
+            continue
+        if g.kind in ("Z", "S", "SDG", "T", "TDG", "P"):
+            f += 6.0 * 0.5 * sel
+        elif g.kind in ("CZ", "CP"):
+            f += 6.0 * 0.25 * sel
+        elif g.kind in ("RZ", "RZZ", "DIAG"):
+            f += 6.0 * sel
+        else:
+            f += 8.0 * 2 ** k * sel
+    return f
+
+
 def measured_traffic(n: int, dtype: str):
     """DRAM bytes per slab-pass launch from the committed ncu summary, scaled by 2^(n - n_capture)
     (every pass streams the whole state once); None if the kernel sources changed since."""
@@ -405,6 +426,7 @@ def run_gpu(args, w, ws, rank, local):
     t_plan = time.perf_counter() - t_plan0
     info = qs.qs_plan_info_get(plan)
     nsteps = info["passes"] + info["remaps"] + info["unblocked"] + info["tc_gates"]
+    plan_fma_per_amp = float(qs.qs_plan_features(plan)[:, 26].sum())
 
     stream = torch.cuda.Stream()
     state = qs.State(n, dtype)
@@ -447,10 +469,14 @@ def run_gpu(args, w, ws, rank, local):
     dom_ms = (st["pass_ms"] + st["remap_ms"] + st["unblocked_ms"]) / max(1, npass_timed)
     peaks = measured_peaks()
     achieved = pass_bytes / (dom_ms / 1e3) / 1e9
-    # arithmetic side: algorithmic flops of the plan (8 * 2^k per amplitude for a dense k-qubit
-    # op, 6 for a diagonal) over the summed pass time, against the FP32 / FP64 ALU peak
+    # arithmetic side: the real FMAs the plan's ops execute per amplitude (2 flops each) over
+    # the summed pass time, against the FP32 / FP64 ALU peak; the circuit's algorithmic flops
+    # (8 * 2^k per amplitude for a dense k-qubit gate, 6 on the amplitudes a diagonal changes)
+    # are reported beside it
     pass_ms_total = st["pass_ms"] + st["remap_ms"] + st["unblocked_ms"]
-    alu_tflops = info["flops_per_amp"] * (1 << n) * args.steps / (pass_ms_total / 1e3) / 1e12
+    exec_flops_amp = 2.0 * float(plan_fma_per_amp)
+    alu_tflops = exec_flops_amp * (1 << n) * args.steps / (pass_ms_total / 1e3) / 1e12
+    algo_flops_amp = circuit_flops_per_amp(gates)
     alu_peak = ALU_PEAK_TFLOPS["c64" if dtype == qs.QS_C64 else "c128"]
     traffic = measured_traffic(n, w["dtype"])
     norm = qs.qs_norm2(state.h)
@@ -508,7 +534,10 @@ def run_gpu(args, w, ws, rank, local):
                      "avg_launch_ms": dom_ms, "bytes_per_launch": pass_bytes},
         "roofline_alu": {"bound": "alu", "achieved": alu_tflops, "peak": alu_peak, "unit": "TFLOP/s",
                          "frac": alu_tflops / alu_peak, "kernel": "slab_pass_kernel",
-                         "flops_per_amp": info["flops_per_amp"],
+                         "executed_flops_per_amp": exec_flops_amp,
+                         "circuit_algorithmic_flops_per_amp": algo_flops_amp,
+                         "circuit_algorithmic_tflops": algo_flops_amp * (1 << n) * args.steps
+                         / (pass_ms_total / 1e3) / 1e12,
                          "peak_source": "152 SMs x 2.07 GHz x (128 FP32 | 2 FP64) FMA/clk x 2"},
         "clocks": clk,
         "gpu_launches": args.steps * nsteps,

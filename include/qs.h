@@ -104,7 +104,11 @@ typedef struct {
     int32_t fuse_force;  /* 1 = merge dense runs up to fuse_width even where the analytic
                             cost model says the wider gate costs more (a learned-planner
                             candidate); 0 = merge only where the model says it pays */
-    int32_t reserved[3];
+    int32_t euler;       /* blocked plans: write complex 1-qubit gates as phase, real rotation,
+                            phase (Z-Y-Z) so that register stages merge the phases.  0 = auto
+                            (complex128 only, whose FP64 pipe bounds the pass), 1 = never,
+                            2 = always */
+    int32_t reserved[2];
 } qs_options;
 
 /* Plan summary (qs_plan_info). */
@@ -305,7 +309,7 @@ qs_status qs_batch_destroy(qs_batch *b);
  * Not in the paper, whose planner is the greedy one (Alg. 1-2).  A 3-layer perceptron (FP32,
  * hidden width 128, ReLU) predicts the device time of one plan step from QS_PLAN_FEATURES
  * numbers that describe it; its forward, backward and Adam kernels are the library's own.
- * The learned planner builds a grid of candidate plans (fusion width, forced or cost-checked
+ * The learned planner builds a grid of candidate plans (Z-Y-Z split or not, fusion width, forced or cost-checked
  * fusion, slab bits, register-stage width), scores every step of every candidate in one
  * batched forward launch, and keeps the candidate with the lowest predicted total.  The greedy
  * plan (the caller's options as given) is the fallback -- it is kept when no candidate is

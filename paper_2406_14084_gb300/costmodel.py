@@ -26,14 +26,15 @@ def max_slab_bits(dtype: int) -> int:
 
 
 def candidate_options(dtype: int, n: int):
-    """The learned planner's grid (fusion width / forced fusion x slab bits x stage bits)."""
+    """The learned planner's grid (Euler split x fusion width / forced fusion x slab bits x stage bits)."""
     bmax = min(max_slab_bits(dtype), n)
     rbmax = 5 if dtype == qs.QS_C64 else 4
     out = []
-    for fw, force in FUSES:
-        for sb in range(max(bmax - 2, 6), bmax + 1):
-            for rb in (rbmax - 1, rbmax):
-                out.append(dict(fuse_width=fw, fuse_force=force, slab_bits=sb, stage_bits=rb))
+    for eu in (1, 2):
+        for fw, force in FUSES:
+            for sb in range(max(bmax - 2, 6), bmax + 1):
+                for rb in (rbmax - 1, rbmax):
+                    out.append(dict(fuse_width=fw, fuse_force=force, slab_bits=sb, stage_bits=rb, euler=eu))
     return out
 
 

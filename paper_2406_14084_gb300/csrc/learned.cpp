@@ -3,10 +3,11 @@
 //
 // The greedy planner (Alg. 1-2 with the analytic op cost) fixes the fusion width, the slab
 // size and the register-stage width from the caller's options.  The learned planner builds a
-// grid of alternatives -- fusion width 1..5 (widths above 2 forced past the analytic check),
-// three slab sizes, two stage widths -- scores every step of every distinct candidate with one
-// batched forward launch, and returns the candidate whose summed prediction is lowest.  The
-// greedy plan is kept unless a candidate is predicted at least 2% faster.
+// grid of alternatives -- Z-Y-Z split of 1-qubit gates on or off, fusion width 1..5 (widths
+// above 2 forced past the analytic check), three slab sizes, two stage widths -- scores every
+// step of every distinct candidate with one batched forward launch, and returns the candidate
+// whose summed prediction is lowest.  The greedy plan is kept unless a candidate is predicted
+// at least 2% faster.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -163,18 +164,20 @@ int learned_choose(const std::vector<CGate> &gates, int n, qs_dtype dt, const qs
     };
     const Fuse fuses[] = {{1, 0}, {2, 0}, {3, 1}, {4, 1}, {5, 1}};
     std::vector<qs_options> cand;
-    for (const Fuse &fz : fuses)
-        for (int sb = std::max(bmax - 2, 6); sb <= bmax; ++sb)
-            for (int rb = rbmax - 1; rb <= rbmax; ++rb) {
-                qs_options o = opt;
-                o.planner = QS_PLANNER_GREEDY;
-                o.fuse_width = fz.width;
-                o.fuse_force = fz.force;
-                o.slab_bits = sb;
-                o.stage_bits = rb;
-                o.slab_mode = QS_SLAB_GATHER;
-                cand.push_back(o);
-            }
+    for (int eu = 1; eu <= 2; ++eu)
+        for (const Fuse &fz : fuses)
+            for (int sb = std::max(bmax - 2, 6); sb <= bmax; ++sb)
+                for (int rb = rbmax - 1; rb <= rbmax; ++rb) {
+                    qs_options o = opt;
+                    o.planner = QS_PLANNER_GREEDY;
+                    o.fuse_width = fz.width;
+                    o.fuse_force = fz.force;
+                    o.slab_bits = sb;
+                    o.stage_bits = rb;
+                    o.slab_mode = QS_SLAB_GATHER;
+                    o.euler = eu;
+                    cand.push_back(o);
+                }
     const size_t nc = cand.size();
     std::vector<Plan> plans(nc);
     std::vector<int> ok(nc, 0);

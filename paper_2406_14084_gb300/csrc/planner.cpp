@@ -300,9 +300,16 @@ double op_cost(const CGate &g, qs_dtype dt)
     const int nc = (int)g.cq.size();
     const double frac = std::ldexp(1.0, -nc);
     switch (g.cls) {
-    case C_DENSE:
+    case C_DENSE: {
+        if (k == 1) {
+            // a real 2x2 matrix acts on real and imaginary parts separately: half the FMAs
+            bool real = true;
+            for (const cd &x : g.m) real = real && x.imag() == 0.0;
+            return frac * w * (real ? 4.0 : 8.0) + 1.0;
+        }
         if (k <= 2) return frac * w * 4.0 * std::ldexp(1.0, k) + 1.0;
         return frac * w * 4.0 * std::ldexp(1.0, k) + smem + 2.0;
+    }
     case C_DIAG: {
         bool cphase = true;
         for (size_t i = 0; i + 1 < g.m.size(); ++i)
@@ -313,7 +320,11 @@ double op_cost(const CGate &g, qs_dtype dt)
             const double flops = (p == cd(-1.0)) ? 0.5 : w * 4.0;  // sign flip vs complex multiply
             return std::ldexp(1.0, -m) * flops + 1.0;
         }
-        if (m <= 7) return w * 4.0 + 2.0;
+        // A table over several qubits costs one multiply per amplitude.  Merging phases of
+        // distinct qubits into one table is left to the register stages, which combine every
+        // register-bit diagonal of a stage into one table at no cost in passes; the extra unit
+        // here keeps the fusion pass from building such tables early.
+        if (m <= 7) return w * 4.0 + 3.0;
         return w * 4.0 + 3.0 * m + smem + 2.0;
     }
     case C_PERMX: return frac * 1.0 + 1.0;
@@ -510,6 +521,67 @@ uint32_t smem_swizzle(uint32_t i, qs_dtype dt)
     return i ^ (((i >> 3) ^ (i >> 6) ^ (i >> 9)) & 7u);
 }
 
+// Split every uncontrolled, complex, non-diagonal 1-qubit gate into Z-Y-Z Euler form,
+//   U = g P(beta) R P(delta),   P(phi) = diag(1, e^{i phi}),   R = [[c, -s], [s, c]] (real),
+// with c = |U00|, s = |U10|, g = U00 / c, e^{i beta} = U10 / (g s), e^{i delta} = -U01 / (g s)
+// (all FP64), and write every uncontrolled 1-qubit diagonal diag(d0, d1) as d0 P(arg d1/d0).
+// The real rotation costs half the FMAs of a complex 2x2, and the phases of all qubits between
+// two layers of rotations commute, so the register stages merge them into one table.  The
+// scalar factors g and d0 are collected into one diagonal placed first (a global phase).
+std::vector<CGate> split_one_qubit(const std::vector<CGate> &in)
+{
+    std::vector<CGate> out;
+    out.reserve(in.size() * 2);
+    cd G = 1.0;
+    for (const CGate &g : in) {
+        if (g.cq.empty() && g.tq.size() == 1 && g.cls == C_DIAG) {
+            const cd d0 = g.m[0], d1 = g.m[1];
+            if (d0 != cd(1.0) && std::abs(d0) > 0.5) {
+                G *= d0;
+                CGate p = g;
+                p.m = {cd(1.0), d1 / d0};
+                out.push_back(std::move(p));
+                continue;
+            }
+        } else if (g.cq.empty() && g.tq.size() == 1 && g.cls == C_DENSE) {
+            bool real = true;
+            for (const cd &x : g.m) real = real && x.imag() == 0.0;
+            const cd u00 = g.m[0], u01 = g.m[1], u10 = g.m[2], u11 = g.m[3];
+            const double c = std::abs(u00), s = std::abs(u10);
+            if (!real && c > 1e-6 && s > 1e-6) {
+                const cd gph = u00 / c;
+                const cd eb = u10 / (gph * s), ed = -u01 / (gph * s);
+                if (std::abs(u11 - gph * eb * ed * c) <= 1e-12) {
+                    G *= gph;
+                    CGate pd, r, pb;
+                    pd.cls = pb.cls = C_DIAG;
+                    pd.tq = pb.tq = r.tq = g.tq;
+                    pd.m = {cd(1.0), ed};
+                    pb.m = {cd(1.0), eb};
+                    pd.nsrc = pb.nsrc = 0;
+                    r.cls = C_DENSE;
+                    r.m = {cd(c), cd(-s), cd(s), cd(c)};
+                    r.nsrc = g.nsrc;
+                    out.push_back(std::move(pd));
+                    out.push_back(std::move(r));
+                    out.push_back(std::move(pb));
+                    continue;
+                }
+            }
+        }
+        out.push_back(g);
+    }
+    if (G != cd(1.0)) {
+        CGate gp;
+        gp.cls = C_DIAG;
+        gp.tq = {0};
+        gp.m = {G, G};
+        gp.nsrc = 0;
+        out.insert(out.begin(), std::move(gp));
+    }
+    return out;
+}
+
 // A diagonal gate whose entries are all 1 except the last one (all qubits 1): Z, S, T, P, CZ,
 // CP and their controlled forms.
 bool controlled_phase(const CGate &g, cd &phase)
@@ -519,6 +591,129 @@ bool controlled_phase(const CGate &g, cd &phase)
         if (g.m[i] != cd(1.0)) return false;
     phase = g.m.back();
     return true;
+}
+
+// Merge the register-bit diagonals of one stage (subs [s0, end)) into as few tables as
+// possible.  A diagonal on register bits commutes with every other diagonal and with every
+// non-diagonal sub whose target bits it does not read, so it may sit anywhere in the interval
+// of positions between the nearest conflicting non-diagonal subs before and after it.  The
+// fewest positions meeting every interval are found by the greedy interval-stabbing rule
+// (sort by right end, place a point at the first uncovered right end).  Each group of two or
+// more diagonals whose element-wise product is cheaper as one table (one complex multiply per
+// amplitude) than as separate subs becomes one SB_DIAG with no outer bits.  Diagonals that
+// read bits outside the registers stay where they are.
+void merge_stage_diagonals(Plan &plan, int s0, int RB, Coefs &cf)
+{
+    const int E = 1 << RB;
+    std::vector<DevSub> in(plan.subs.begin() + s0, plan.subs.end());
+    const int ns = (int)in.size();
+    auto target_bits = [](const DevSub &s) -> uint32_t {
+        switch (s.type) {
+        case SB_G1: case SB_G1R: case SB_X: return 1u << s.j0;
+        case SB_G2: case SB_SWAP: return (1u << s.j0) | (1u << s.j1);
+        default: return 0;
+        }
+    };
+    auto is_diag = [](const DevSub &s) { return s.type == SB_PHASE || s.type == SB_DIAG; };
+    auto eligible = [](const DevSub &s) {
+        return (s.type == SB_PHASE && s.lcm == 0 && s.ocm == 0) || (s.type == SB_DIAG && s.ndl == 0);
+    };
+    std::vector<std::vector<cd>> tab(ns);
+    std::vector<uint32_t> reads(ns, 0);
+    std::vector<double> cost(ns, 0.0);
+    std::vector<int> slot(ns, 0), nd_index;  // nd_index: positions of non-diagonal subs
+    for (int i = 0; i < ns; ++i) {
+        slot[i] = (int)nd_index.size();
+        if (!is_diag(in[i])) {
+            nd_index.push_back(i);
+            continue;
+        }
+        if (!eligible(in[i])) continue;
+        std::vector<cd> t(E, cd(1.0));
+        if (in[i].type == SB_PHASE) {
+            const cd p = plan.coef[in[i].mat];
+            for (int e = 0; e < E; ++e)
+                if ((uint32_t(e) & in[i].scm) == in[i].scm) t[e] = p;
+            const double frac = std::ldexp(1.0, -__builtin_popcount(in[i].scm));
+            cost[i] = E * frac * (p == cd(-1.0) ? 0.25 : 1.0);
+        } else {
+            for (int e = 0; e < E; ++e) t[e] = plan.coef[in[i].mat + e];
+            cost[i] = E;
+        }
+        for (int j = 0; j < RB; ++j)
+            for (int e = 0; e < E; ++e)
+                if (t[e] != t[e ^ (1 << j)]) {
+                    reads[i] |= 1u << j;
+                    break;
+                }
+        tab[i] = std::move(t);
+    }
+    const int m = (int)nd_index.size();
+    // feasible slot interval [lo, hi] of each eligible diagonal
+    std::vector<int> lo(ns, 0), hi(ns, m), cand;
+    for (int i = 0; i < ns; ++i) {
+        if (tab[i].empty()) continue;
+        for (int k = 0; k < slot[i]; ++k)
+            if (target_bits(in[nd_index[k]]) & reads[i]) lo[i] = k + 1;
+        for (int k = slot[i]; k < m; ++k)
+            if (target_bits(in[nd_index[k]]) & reads[i]) {
+                hi[i] = k;
+                break;
+            }
+        cand.push_back(i);
+    }
+    std::sort(cand.begin(), cand.end(), [&](int a, int b) { return hi[a] < hi[b] || (hi[a] == hi[b] && a < b); });
+    std::vector<int> point(ns, -1);
+    std::vector<std::vector<int>> groups;
+    std::vector<int> gpoint;
+    for (int i : cand) {
+        if (point[i] >= 0) continue;
+        const int p = hi[i];
+        std::vector<int> gr;
+        for (int j : cand)
+            if (point[j] < 0 && lo[j] <= p && p <= hi[j]) {
+                point[j] = p;
+                gr.push_back(j);
+            }
+        groups.push_back(gr);
+        gpoint.push_back(p);
+    }
+    std::vector<char> merged(ns, 0);
+    std::vector<std::vector<DevSub>> at(m + 1);
+    bool changed = false;
+    for (size_t gi = 0; gi < groups.size(); ++gi) {
+        const std::vector<int> &gr = groups[gi];
+        double c = 0;
+        for (int i : gr) c += cost[i];
+        if (gr.size() < 2 || c <= 1.25 * E) continue;
+        std::vector<cd> t(E, cd(1.0));
+        for (int i : gr) {
+            for (int e = 0; e < E; ++e) t[e] *= tab[i][e];
+            merged[i] = 1;
+        }
+        DevSub s;
+        std::memset(&s, 0, sizeof s);
+        s.type = SB_DIAG;
+        s.ndl = 0;
+        s.mat = cf.push(t);
+        at[gpoint[gi]].push_back(s);
+        changed = true;
+    }
+    if (!changed) return;
+    std::vector<DevSub> out;
+    int k = 0;
+    for (int i = 0; i < ns; ++i) {
+        if (!is_diag(in[i])) {
+            for (const DevSub &s : at[k]) out.push_back(s);
+            ++k;
+            out.push_back(in[i]);
+            continue;
+        }
+        if (!merged[i]) out.push_back(in[i]);
+    }
+    for (const DevSub &s : at[m]) out.push_back(s);
+    plan.subs.resize(s0);
+    plan.subs.insert(plan.subs.end(), out.begin(), out.end());
 }
 
 // Split a pass's scheduled ops into register stages (Alg. 2's innermost fusion level applied
@@ -708,6 +903,7 @@ void build_stages(Plan &plan, const std::vector<CGate> &gates, const std::vector
             }
             plan.subs.push_back(s);
         }
+        merge_stage_diagonals(plan, st.sub_begin, RB, cf);
         st.sub_end = (int)plan.subs.size();
         DevOp op;
         std::memset(&op, 0, sizeof op);
@@ -1041,6 +1237,8 @@ int build_plan(const std::vector<CGate> &gates_in, int n, qs_dtype dt, const qs_
         gates = fuse_pass(gates, kdiag, kTcTargets, true, false, dt);
         for (const CGate &g : gates) is_tc.push_back(g.cls == C_DENSE && g.tq.size() >= 4);
     } else if (opt.fuse_width > 0) {
+        const bool euler = opt.euler == 2 || (opt.euler == 0 && dt == QS_C128);
+        if (opt.blocking && euler) gates = split_one_qubit(gates);
         const int kdiag = opt.diag_bits > 0 ? std::min(opt.diag_bits, kMaxDiagBits) : 10;
         int kdense = std::min(opt.fuse_width, kMaxDense);
         if (opt.blocking) kdense = std::min(kdense, lowblock ? b : std::max(1, b - lo));

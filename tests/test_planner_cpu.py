@@ -224,3 +224,52 @@ def test_tensor_core_mode_rejections():
     with pytest.raises(qs.QsError) as e:
         qs.qs_fuse(W.layered(10, 2, 1), 10, qs.options(tc=qs.QS_TC_BF16X3, dtype=qs.QS_C64))
     assert e.value.status == qs.QS_EUNSUPPORTED
+
+
+@pytest.mark.parametrize("dtype,stage", [(qs.QS_C64, 5), (qs.QS_C64, 4), (qs.QS_C128, 4), (qs.QS_C128, 3)])
+def test_euler_split_and_stage_diagonal_tables(dtype, stage):
+    """Complex 1-qubit gates become a real rotation between two phases; the phases and CZ signs
+    of a stage merge into register-bit tables.  The replayed plan still equals the oracle."""
+    n = 12
+    g = W.layered(n, 8, 2024)
+    info, stats = check_plan(g, n, qs.options(slab_bits=9, seg_bits=3, dtype=dtype, stage_bits=stage, euler=2), seed=3)
+    p = qs.qs_fuse(g, n, qs.options(slab_bits=9, seg_bits=3, dtype=dtype, stage_bits=stage, euler=2))
+    try:
+        X = qs.qs_plan_features(p)
+    finally:
+        qs.qs_plan_destroy(p)
+    assert X[:, 16].sum() <= 1        # complex 2x2 in stages: at most the global-phase carrier
+    assert X[:, 16].sum() + X[:, 17].sum() >= n * 8  # one rotation per U3 (one carries the phase)
+    assert X[:, 20].sum() >= 1        # merged register-bit diagonal tables
+
+
+def test_euler_split_of_generic_unitaries_and_rz():
+    n = 10
+    rng = W.SplitMix64(5)
+    gates = []
+    for i in range(60):
+        q = rng.below(n)
+        r = rng.below(4)
+        if r == 0:
+            gates.append(Gate("UNITARY", (q,), (), (), W.random_unitary(1, 900 + i)))
+        elif r == 1:
+            gates.append(Gate("RZ", (q,), (), (rng.angle(),)))
+        elif r == 2:
+            gates.append(Gate("RX", (q,), (), (rng.angle(),)))
+        else:
+            a, b = rng.distinct(n, 2)
+            gates.append(Gate("CZ", (a, b)))
+    for dtype in (qs.QS_C64, qs.QS_C128):
+        check_plan(gates, n, qs.options(slab_bits=7, seg_bits=2, dtype=dtype, euler=2), seed=4)
+
+
+def test_euler_default_follows_precision():
+    g = W.layered(12, 4, 7)
+    counts = {}
+    for dtype in (qs.QS_C64, qs.QS_C128):
+        for eu in (0, 1, 2):
+            p = qs.qs_fuse(g, 12, qs.options(dtype=dtype, euler=eu, slab_bits=9, seg_bits=3))
+            counts[dtype, eu] = qs.qs_plan_features(p)[:, 17].sum()  # real 1-qubit rotations
+            qs.qs_plan_destroy(p)
+    assert counts[qs.QS_C64, 0] == counts[qs.QS_C64, 1] == 0
+    assert counts[qs.QS_C128, 0] == counts[qs.QS_C128, 2] > 0 and counts[qs.QS_C128, 1] == 0
