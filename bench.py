@@ -176,6 +176,22 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def max_over_ranks(value: float, dist=None, device: str = "cpu") -> float:
+    """The slowest rank's time: every replica's timed region is over only when all are."""
+    if dist is None:
+        return value
+    import torch
+
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(units_per_rank: int, steps: int, ms_max: float, world: int) -> float:
+    """Whole-job rate of `world` independent replicas: all units over the slowest rank's time."""
+    return world * units_per_rank * steps / (ms_max / 1e3)
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -456,12 +472,9 @@ def run_gpu(args, w, ws, rank, local):
     qs.qs_set_profiling(state.h, False)
     ms = ev0.elapsed_time(ev1)
     st = qs.qs_stats(state.h)
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist, "cuda")
     ms_step = ms / args.steps
-    gates_per_s = ws * len(gates) * args.steps / (ms / 1e3)
+    gates_per_s = replica_throughput(len(gates), args.steps, ms, ws)
     pass_bytes = 2.0 * (1 << n) * amp_bytes
     passes_per_step = info["passes"] + info["remaps"] + info["unblocked"]
     eff_gbs = passes_per_step * pass_bytes / (ms_step / 1e3) / 1e9
