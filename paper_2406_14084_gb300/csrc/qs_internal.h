@@ -78,7 +78,9 @@ enum SubType : uint8_t {
     SB_G1R = 6,    // 2x2 matrix with real entries on register bit j0
 };
 
-struct DevSub {
+// 48 bytes, 16-byte aligned: the kernels fetch the first 24 bytes with one 16-byte and one
+// 8-byte load (the byte order of the first word -- type, j0, j1, ndl -- is relied upon).
+struct alignas(16) DevSub {
     uint8_t type;
     uint8_t j0, j1;
     uint8_t ndl;       // SB_DIAG: non-register table bits
@@ -92,6 +94,7 @@ struct DevSub {
     uint8_t dl[12];
     uint8_t pad[4];
 };
+static_assert(sizeof(DevSub) == 48, "DevSub layout");
 
 struct DevStage {
     uint8_t r;          // register bits

@@ -217,16 +217,34 @@ __device__ __forceinline__ void sub_swap(C (&v)[1 << RB], uint32_t scm)
     }
 }
 
-template <typename C, int RB>
-__device__ __forceinline__ void apply_sub(C (&v)[1 << RB], const DevSub &s, uint32_t gbase,
-                                          uint64_t cta_base, const C *__restrict__ coef)
+// Index of the lowest set bit of i > 0 (folds to a constant in unrolled loops).
+__device__ __forceinline__ int lowest_bit(int i) { return __ffs(i) - 1; }
+
+// The first 24 bytes of a DevSub, fetched as one 16-byte and one 8-byte load.
+struct SubHead {
+    uint32_t w0;   // type | j0 << 8 | j1 << 16 | ndl << 24
+    uint32_t scm, lcm, mat;
+    uint64_t ocm;
+};
+
+__device__ __forceinline__ SubHead load_sub_head(const DevSub *__restrict__ p)
 {
-    if ((gbase & s.lcm) != s.lcm || (cta_base & s.ocm) != s.ocm) return;
-    const C *__restrict__ M = coef + s.mat;
-    const uint32_t scm = s.scm;
-    switch (s.type) {
+    const uint4 a = __ldg(reinterpret_cast<const uint4 *>(p));
+    const unsigned long long o = __ldg(reinterpret_cast<const unsigned long long *>(p) + 2);
+    return SubHead{a.x, a.y, a.z, a.w, o};
+}
+
+template <typename C, int RB>
+__device__ __forceinline__ void apply_sub(C (&v)[1 << RB], const SubHead &h, const DevSub *__restrict__ sp,
+                                          uint32_t gbase, uint64_t cta_base, const C *__restrict__ coef)
+{
+    if ((gbase & h.lcm) != h.lcm || (cta_base & h.ocm) != h.ocm) return;
+    const C *__restrict__ M = coef + h.mat;
+    const uint32_t scm = h.scm;
+    const uint32_t type = h.w0 & 0xffu, j0 = (h.w0 >> 8) & 0xffu, j1 = (h.w0 >> 16) & 0xffu, ndl = h.w0 >> 24;
+    switch (type) {
     case SB_G1:
-        switch (s.j0) {
+        switch (j0) {
         case 0: sub_g1<C, RB, 0>(v, M, scm); break;
         case 1: sub_g1<C, RB, 1>(v, M, scm); break;
         case 2: sub_g1<C, RB, 2>(v, M, scm); break;
@@ -236,7 +254,7 @@ __device__ __forceinline__ void apply_sub(C (&v)[1 << RB], const DevSub &s, uint
         }
         break;
     case SB_G2:
-        switch (s.j0 * 8 + s.j1) {
+        switch (j0 * 8 + j1) {
         case 0 * 8 + 1: sub_g2<C, RB, 0, 1>(v, M, scm); break;
         case 0 * 8 + 2: sub_g2<C, RB, 0, 2>(v, M, scm); break;
         case 0 * 8 + 3: sub_g2<C, RB, 0, 3>(v, M, scm); break;
@@ -251,7 +269,7 @@ __device__ __forceinline__ void apply_sub(C (&v)[1 << RB], const DevSub &s, uint
         }
         break;
     case SB_X:
-        switch (s.j0) {
+        switch (j0) {
         case 0: sub_x<C, RB, 0>(v, scm); break;
         case 1: sub_x<C, RB, 1>(v, scm); break;
         case 2: sub_x<C, RB, 2>(v, scm); break;
@@ -261,7 +279,7 @@ __device__ __forceinline__ void apply_sub(C (&v)[1 << RB], const DevSub &s, uint
         }
         break;
     case SB_SWAP:
-        switch (s.j0 * 8 + s.j1) {
+        switch (j0 * 8 + j1) {
         case 0 * 8 + 1: sub_swap<C, RB, 0, 1>(v, scm); break;
         case 0 * 8 + 2: sub_swap<C, RB, 0, 2>(v, scm); break;
         case 0 * 8 + 3: sub_swap<C, RB, 0, 3>(v, scm); break;
@@ -316,7 +334,7 @@ __device__ __forceinline__ void apply_sub(C (&v)[1 << RB], const DevSub &s, uint
         break;
     }
     case SB_G1R:
-        switch (s.j0) {
+        switch (j0) {
         case 0: sub_g1r<C, RB, 0>(v, M, scm); break;
         case 1: sub_g1r<C, RB, 1>(v, M, scm); break;
         case 2: sub_g1r<C, RB, 2>(v, M, scm); break;
@@ -327,8 +345,8 @@ __device__ __forceinline__ void apply_sub(C (&v)[1 << RB], const DevSub &s, uint
         break;
     case SB_DIAG: {
         uint32_t hi = 0;
-        for (int j = 0; j < s.ndl; ++j) {
-            const uint32_t src = s.dl[j];
+        for (int j = 0; j < int(ndl); ++j) {
+            const uint32_t src = sp->dl[j];
             const uint32_t bit = (src & 0x80) ? uint32_t((cta_base >> (src & 0x7f)) & 1)
                                               : ((gbase >> src) & 1u);
             hi |= bit << j;
@@ -348,20 +366,56 @@ __device__ __noinline__ void run_stage(C *sm, const DevStage *__restrict__ stg,
                                           uint64_t cta_base, uint32_t tid, uint32_t nthr)
 {
     constexpr int E = 1 << RB;
-    const int nrest = stg->nrest;
+    constexpr int SW = sizeof(C) == 8 ? 1 : 2;
+    // bytes 0..7: r, nrest, sbits[0..5] (register bits in ascending slab-local order)
+    const uint2 hd = __ldg(reinterpret_cast<const uint2 *>(stg));
+    const uint2 rng = __ldg(reinterpret_cast<const uint2 *>(&stg->sub_begin));
+    const int nrest = (hd.x >> 8) & 0xff;
+    uint32_t sb[RB], bo[RB];
+#pragma unroll
+    for (int j = 0; j < RB; ++j) {
+        sb[j] = j < 2 ? (hd.x >> (16 + 8 * j)) & 0xff : (hd.y >> (8 * (j - 2))) & 0xff;
+        // the swizzle is linear over GF(2): the offset of register index e is the XOR of the
+        // swizzled single-bit offsets of its set bits
+        bo[j] = swz<SW>(1u << sb[j]);
+    }
     const uint32_t ngroups = 1u << nrest;
-    const int s0 = stg->sub_begin, s1 = stg->sub_end;
+    const int s0 = int(rng.x), s1 = int(rng.y);
     for (uint32_t g = tid; g < ngroups; g += nthr) {
-        uint32_t base = 0;
-        for (int j = 0; j < nrest; ++j) base |= ((g >> j) & 1u) << stg->rest[j];
-        // off[e] holds swizzled offsets; the swizzle is linear, so one XOR per element
-        const uint32_t pb = swz<(sizeof(C) == 8 ? 1 : 2)>(base);
+        // slab index of the group: g's bits with zeros inserted at the register bits
+        uint32_t base = g;
+#pragma unroll
+        for (int j = 0; j < RB; ++j) {
+            const uint32_t low = base & ((1u << sb[j]) - 1u);
+            base = ((base ^ low) << 1) | low;
+        }
+        const uint32_t pb = swz<SW>(base);
         C v[E];
+        // visit the elements in Gray-code order: one XOR of the address per element
+        {
+            uint32_t a = pb;
 #pragma unroll
-        for (int e = 0; e < E; ++e) v[e] = sm[pb ^ stg->off[e]];
-        for (int s = s0; s < s1; ++s) apply_sub<C, RB>(v, subs[s], base, cta_base, coef);
+            for (int i = 0; i < E; ++i) {
+                if (i) a ^= bo[lowest_bit(i)];
+                v[i ^ (i >> 1)] = sm[a];
+            }
+        }
+        if (s0 < s1) {
+            SubHead nxt = load_sub_head(subs + s0);
+            for (int s = s0; s < s1; ++s) {
+                const SubHead cur = nxt;
+                if (s + 1 < s1) nxt = load_sub_head(subs + s + 1);
+                apply_sub<C, RB>(v, cur, subs + s, base, cta_base, coef);
+            }
+        }
+        {
+            uint32_t a = pb;
 #pragma unroll
-        for (int e = 0; e < E; ++e) sm[pb ^ stg->off[e]] = v[e];
+            for (int i = 0; i < E; ++i) {
+                if (i) a ^= bo[lowest_bit(i)];
+                sm[a] = v[i ^ (i >> 1)];
+            }
+        }
     }
 }
 
