@@ -15,8 +15,10 @@
 // 128-byte-swizzled K-major operand layout -> 24 tcgen05.mma (3 products x 8 K-steps of 16)
 // issued by one thread into a 128-lane x 128-column FP32 accumulator in TMEM ->
 // tcgen05.commit to an mbarrier -> tcgen05.ld of the accumulator by the 4 warps (warp w owns
-// TMEM lanes 32w..32w+31 = rows) -> back into the slab -> 16-byte stores.  The E operand stays
-// in shared memory for the whole launch.  Every mbarrier wait is bounded; on expiry the CTA
+// TMEM lanes 32w..32w+31 = rows) -> into the (now free) A operand region -> 16-byte stores.
+// The next slab's gather is issued as soon as the split has read the slab buffer, so it
+// overlaps the MMAs, the accumulator read-back and the stores.  The E operand stays in shared
+// memory for the whole launch.  Every mbarrier wait is bounded; on expiry the CTA
 // records QS_ETIMEOUT, releases its tensor memory and exits.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -28,7 +30,7 @@
 namespace qs {
 namespace {
 
-constexpr int kThreads = 128;
+constexpr int kThreads = 256;  // 8 warps: two per TMEM lane quarter
 constexpr uint32_t kOpBytes = kTcRows * kTcK * 2;  // one BF16 operand: 128 x 128 x 2 = 32 KiB
 constexpr uint32_t kSlabBytes = (1u << kTcSlabBits) * 8;
 constexpr uint32_t kOffAhi = kSlabBytes, kOffAlo = kOffAhi + kOpBytes, kOffBhi = kOffAlo + kOpBytes,
@@ -51,6 +53,8 @@ __device__ __forceinline__ void cp_async16(uint32_t dst, const void *src)
 {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
 }
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 
 __device__ __forceinline__ void cp_async_wait_all()
 {
@@ -204,25 +208,36 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint32_t phase = 0;
     bool failed = false;
 
-    for (uint64_t s = blockIdx.x; s < nslabs; s += gridDim.x) {
+    auto slab_ptr = [&](uint64_t s) -> float2 * {
         uint64_t gb = s << lo;
         for (int m = 0; m < nhi; ++m) {
             const uint64_t lowm = (1ull << P.hipos[m]) - 1;
             gb = ((gb & ~lowm) << 1) | (gb & lowm);
         }
-        float2 *g = state + gb;
+        return state + gb;
+    };
+    auto issue_load = [&](const float2 *g) {
         for (uint32_t v = tid; v < nvec; v += kThreads) {
             const uint32_t seg = v >> vps_log, w = v & ((1u << vps_log) - 1);
             const uint64_t so = K.seg_lo[seg & 63] | K.seg_hi[(seg >> 6) & 63];
             cp_async16(saddr(slab) + 16u * v, reinterpret_cast<const uint4 *>(g + so) + w);
         }
+        cp_async_commit();
+    };
+    // Results go to the operand region A (64 KiB, free once the MMAs have completed) so that the
+    // next slab can stream into the slab buffer while this one is multiplied and stored.
+    float2 *res = reinterpret_cast<float2 *>(base + kOffAhi);
+    if (uint64_t(blockIdx.x) < nslabs) issue_load(slab_ptr(blockIdx.x));
+    for (uint64_t s = blockIdx.x; s < nslabs; s += gridDim.x) {
+        float2 *g = slab_ptr(s);
         cp_async_wait_all();
         __syncthreads();
         // split row m = tid into BF16 hi / lo in the swizzled operand layout (16-byte chunks of 8)
         {
-            const uint32_t m = tid, mo = K.moff[m];
+            // thread (m, half): row m, 16-byte chunks half*8 .. half*8+7 of its 16
+            const uint32_t m = tid & 127u, mo = K.moff[m], c16b = (tid >> 7) * (kTcK / 16);
 #pragma unroll 2
-            for (uint32_t c16 = 0; c16 < kTcK / 8; ++c16) {
+            for (uint32_t c16 = c16b; c16 < c16b + kTcK / 16; ++c16) {
                 __nv_bfloat162 h[4], l[4];
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
@@ -239,6 +254,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         fence_proxy_async();
         __syncthreads();
+        // the slab buffer has been read: prefetch this CTA's next slab into it
+        if (s + gridDim.x < nslabs) issue_load(slab_ptr(s + gridDim.x));
         if (tid == 0) {
             tc_fence_after();
             // D = A_hi E_hi^T + A_hi E_lo^T + A_lo E_hi^T over 8 K-steps of 16 elements
@@ -262,15 +279,16 @@ __global__ void __launch_bounds__(kThreads, 1)
             break;
         }
         tc_fence_after();
-        // epilogue: warp w reads rows 32w..32w+31 (its TMEM lane quarter), 32 columns at a time
+        // epilogue: warp w reads rows 32q..32q+31 of its TMEM lane quarter q = w % 4, columns
+        // 64h..64h+63 with h = w / 4, 32 columns at a time
         {
-            const uint32_t m = warp * 32 + lane, mo = K.moff[m];
+            const uint32_t q4 = warp & 3u, m = q4 * 32 + lane, mo = K.moff[m], cb = (warp >> 2) * (kTcK / 2);
 #pragma unroll 1
-            for (uint32_t c0 = 0; c0 < kTcK; c0 += 32) {
+            for (uint32_t c0 = cb; c0 < cb + kTcK / 2; c0 += 32) {
                 float r[32];
-                tmem_ld32(tmem + ((warp * 32u) << 16) + c0, r);
+                tmem_ld32(tmem + ((q4 * 32u) << 16) + c0, r);
 #pragma unroll
-                for (int q = 0; q < 16; ++q) slab[mo | K.joff[c0 / 2 + q]] = make_float2(r[2 * q], r[2 * q + 1]);
+                for (int q = 0; q < 16; ++q) res[mo | K.joff[c0 / 2 + q]] = make_float2(r[2 * q], r[2 * q + 1]);
             }
         }
         tc_fence_before();
@@ -278,10 +296,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (uint32_t v = tid; v < nvec; v += kThreads) {
             const uint32_t seg = v >> vps_log, w = v & ((1u << vps_log) - 1);
             const uint64_t so = K.seg_lo[seg & 63] | K.seg_hi[(seg >> 6) & 63];
-            __stcs(reinterpret_cast<float4 *>(g + so) + w, reinterpret_cast<const float4 *>(slab)[v]);
+            __stcs(reinterpret_cast<float4 *>(g + so) + w, reinterpret_cast<const float4 *>(res)[v]);
         }
-        __syncthreads();
+        __syncthreads();  // the operand region is rewritten by the next split
     }
+    cp_async_wait_all();  // no copy may land after the CTA has left (timeout path)
     (void)failed;
     tc_fence_before();
     __syncthreads();

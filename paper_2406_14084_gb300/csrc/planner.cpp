@@ -1231,8 +1231,10 @@ int build_plan(const std::vector<CGate> &gates_in, int n, qs_dtype dt, const qs_
     std::vector<char> is_tc;
     if (tc) {
         // Alg. 2 level 3 with F = 6: merge greedily into dense blocks of at most 6 qubits; the
-        // products are FP64 on the host.  Blocks of 4+ qubits run on the tensor cores.
-        const int kdiag = opt.diag_bits > 0 ? std::min(opt.diag_bits, kMaxDiagBits) : 10;
+        // products are FP64 on the host.  Blocks of 4+ qubits run on the tensor cores.  Diagonal
+        // runs are merged no wider than the blocks by default: wider tables could not join a
+        // 6-qubit block and would each cost a separate pass.
+        const int kdiag = opt.diag_bits > 0 ? std::min(opt.diag_bits, kMaxDiagBits) : kTcTargets;
         gates = fuse_pass(gates, kdiag, 0, false, true, dt);
         gates = fuse_pass(gates, kdiag, kTcTargets, true, false, dt);
         for (const CGate &g : gates) is_tc.push_back(g.cls == C_DENSE && g.tq.size() >= 4);
