@@ -42,6 +42,7 @@ WORKLOADS = {
     "layered28_c64": dict(n=28, dtype="c64", kind="layered", depth=40, seed=1002),
     "precision33_c64": dict(n=33, dtype="c64", kind="layered", depth=60, seed=1003, tc=True),
     "precision30_c64": dict(n=30, dtype="c64", kind="layered", depth=60, seed=1003, tc=True),
+    "precision28_c64": dict(n=28, dtype="c64", kind="layered", depth=60, seed=1003, tc=True),
     "config1": dict(n=20, dtype="c128", kind="random", ngates=200, seed=1001),
     "batch1024_c64": dict(n=24, dtype="c64", kind="batch", count=1024, seed=1004),
     "batch1024_c128": dict(n=24, dtype="c128", kind="batch", count=1024, seed=1004),
@@ -515,6 +516,7 @@ def run_gpu(args, w, ws, rank, local):
     exec_flops_amp = 2.0 * float(plan_fma_per_amp)
     alu_tflops = exec_flops_amp * (1 << n) * args.steps / (pass_ms_total / 1e3) / 1e12
     algo_flops_amp = circuit_flops_per_amp(gates)
+    traffic = measured_traffic(n, w["dtype"])
     roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
             "kernel": "slab_pass_kernel", "peak_source": peaks["source"],
@@ -533,7 +535,6 @@ def run_gpu(args, w, ws, rank, local):
                    "frac": tc_tflops / peaks["bf16_tflops"], "kernel": "tc_bf16_kernel",
                    "peak_source": "BF16 dense, " + peaks["source"]}
     alu_peak = ALU_PEAK_TFLOPS["c64" if dtype == qs.QS_C64 else "c128"]
-    traffic = measured_traffic(n, w["dtype"])
     norm = qs.qs_norm2(state.h)
     fidelity = None if args.no_fidelity else fidelity_check(w, opts, dtype)
     fidelity_fp64 = fidelity_vs_fp64_path(w, opts) if (opts.tc and not args.no_fidelity) else None
