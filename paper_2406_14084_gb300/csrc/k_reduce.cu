@@ -12,7 +12,9 @@
 // memory owned by the state.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdio>
+#include <cstring>
 #include <mutex>
 #include <vector>
 
@@ -163,6 +165,92 @@ __global__ void __launch_bounds__(kRedThreads) expect_kernel(const typename Cx<R
     }
 }
 
+// Term parities as a linear map.  For a group of Z strings with the same X mask, the sign of term
+// t at index x is (-1)^{p_t(x)} with p_t(x) = popcount(x & zm_t) mod 2, linear over GF(2) in x:
+// the parity vector p(x) (one bit per term) is the XOR of the columns col[i] of the bits i set
+// in x.  With h(x) = sum_t c_t (-1)^{p_t} = sum_t c_t - 2 sum_{t : p_t = 1} c_t, the second sum
+// is read from byte tables: tab[b][v] = sum of c_{8b+k} over the set bits k of v.
+constexpr int kParityMaxTerms = 128;
+constexpr int kParityBytes = kParityMaxTerms / 8;
+struct ParityTables {
+    uint32_t col[64][kParityMaxTerms / 32];  // parity columns of the physical bits
+    double csum_re, csum_im;                 // sum of all coefficients
+    int nbytes;                              // table bytes in use
+    int pad;
+    double tre[kParityBytes][256], tim[kParityBytes][256];
+};
+
+// Each block owns 2^(8 + klog) consecutive amplitudes; thread t visits lo | (gray(i) << 8) | t for
+// i = 0 .. 2^klog - 1, so consecutive visits differ in one index bit and the parity vector
+// changes by one column (one XOR per word); the warp's 32 amplitudes stay contiguous.
+template <typename R>
+__global__ void __launch_bounds__(kRedThreads) expect_parity_kernel(const typename Cx<R>::T *__restrict__ a,
+                                                                    uint64_t xm, int klog,
+                                                                    const ParityTables *__restrict__ pt,
+                                                                    double *__restrict__ part)
+{
+    constexpr int NW = kParityMaxTerms / 32;
+    extern __shared__ __align__(16) unsigned char dyn[];
+    R *tre = reinterpret_cast<R *>(dyn);
+    const int nb = pt->nbytes;
+    R *tim = tre + nb * 256;
+    __shared__ uint32_t col[64][NW];
+    for (int j = threadIdx.x; j < nb * 256; j += blockDim.x) {
+        tre[j] = (R)pt->tre[j >> 8][j & 255];
+        tim[j] = (R)pt->tim[j >> 8][j & 255];
+    }
+    for (int j = threadIdx.x; j < 64 * NW; j += blockDim.x) col[j / NW][j % NW] = pt->col[j / NW][j % NW];
+    __syncthreads();
+    const R cre0 = (R)pt->csum_re, cim0 = (R)pt->csum_im;
+    const uint64_t lo = uint64_t(blockIdx.x) << (8 + klog);
+    const uint64_t x0 = lo | threadIdx.x;
+    uint32_t P[NW];
+#pragma unroll
+    for (int w = 0; w < NW; ++w) P[w] = 0;
+    for (int i = 0; i < 64; ++i)
+        if (x0 >> i & 1)
+#pragma unroll
+            for (int w = 0; w < NW; ++w) P[w] ^= col[i][w];
+    double accr = 0.0, acci = 0.0;
+    R fr = 0, fi = 0;
+    int cnt = 0;
+    const uint32_t K = 1u << klog;
+    for (uint32_t i = 0; i < K; ++i) {
+        if (i) {
+            const int bit = 8 + __ffs(i) - 1;
+#pragma unroll
+            for (int w = 0; w < NW; ++w) P[w] ^= col[bit][w];
+        }
+        const uint64_t x = x0 | (uint64_t(i ^ (i >> 1)) << 8);
+        const auto ax = a[x];
+        const auto ay = a[x ^ xm];
+        const R vr = (R)ay.x * (R)ax.x + (R)ay.y * (R)ax.y;
+        const R vi = (R)ay.x * (R)ax.y - (R)ay.y * (R)ax.x;
+        R sr = 0, si = 0;
+        for (int b = 0; b < nb; ++b) {
+            const uint32_t v = (P[b >> 2] >> (8 * (b & 3))) & 0xffu;
+            sr += tre[b * 256 + v];
+            si += tim[b * 256 + v];
+        }
+        const R er = cre0 - R(2) * sr, ei = cim0 - R(2) * si;
+        fr += er * vr - ei * vi;
+        fi += er * vi + ei * vr;
+        if (sizeof(R) == 4 && ++cnt == 32) {
+            accr += (double)fr;
+            acci += (double)fi;
+            fr = fi = 0;
+            cnt = 0;
+        }
+    }
+    accr += (double)fr;
+    acci += (double)fi;
+    block_sum2(accr, acci);
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = accr;
+        part[gridDim.x + blockIdx.x] = acci;
+    }
+}
+
 // Marginal probabilities: hist[m] += |a_x|^2 with m gathered from the bits pos[0..nq).
 template <typename R>
 __global__ void __launch_bounds__(kRedThreads) probs_kernel(const typename Cx<R>::T *__restrict__ a,
@@ -227,8 +315,8 @@ int cuda_fail(const char *what, char *err, size_t errlen)
 
 size_t reduce_scratch_bytes()
 {
-    // partials (2 x blocks) + 2 results + one term group
-    return sizeof(double) * (2 * kRedBlocksMax + 8) + sizeof(TermGroup) + 256;
+    // partials (2 x blocks) + 2 results + one term group + its parity tables
+    return sizeof(double) * (2 * kRedBlocksMax + 8) + sizeof(TermGroup) + 256 + sizeof(ParityTables) + 256;
 }
 
 int launch_norm2(const LaunchCtx &c, double *d_scratch, double *h_out, char *err, size_t errlen)
@@ -296,6 +384,9 @@ int launch_expect(const LaunchCtx &c, const uint64_t *xm, const uint64_t *zm, co
     const int blocks = reduce_blocks(N);
     std::vector<TermGroup> hgv(1);  // host staging; each copy completes before reuse
     TermGroup &hg = hgv[0];
+    std::vector<ParityTables> hpt(1);
+    ParityTables *dpt = reinterpret_cast<ParityTables *>(
+        (reinterpret_cast<uintptr_t>(dgrp) + sizeof(TermGroup) + 255) & ~uintptr_t(255));
     double tot_r = 0.0, tot_i = 0.0;
     std::vector<char> done(nterms, 0);
     for (size_t i = 0; i < nterms; ++i) {
@@ -313,14 +404,57 @@ int launch_expect(const LaunchCtx &c, const uint64_t *xm, const uint64_t *zm, co
             hg.cim[hg.nterms] = coeff[j] * pi[ny];
             hg.nterms++;
         }
-        if (cudaMemcpyAsync(dgrp, &hg, sizeof(TermGroup), cudaMemcpyHostToDevice, st) != cudaSuccess)
-            return cuda_fail("expect upload", err, errlen);
-        if (c.dt == QS_C64)
-            expect_kernel<float><<<blocks, kRedThreads, 0, st>>>((const float2 *)c.amp, N, dgrp, part);
-        else
-            expect_kernel<double><<<blocks, kRedThreads, 0, st>>>((const double2 *)c.amp, N, dgrp,
-                                                                  part);
-        finish_kernel<<<1, kRedThreads, 0, st>>>(part, blocks, blocks, res);
+        int nblk = blocks;
+        if (hg.nterms >= 8 && hg.nterms <= kParityMaxTerms && c.n >= 16) {
+            // parity tables (host, FP64), then the Gray-walk kernel
+            ParityTables &pt = hpt[0];
+            std::memset(&pt, 0, sizeof pt);
+            pt.nbytes = (hg.nterms + 7) / 8;
+            for (int t = 0; t < hg.nterms; ++t) {
+                pt.csum_re += hg.cre[t];
+                pt.csum_im += hg.cim[t];
+                for (int i = 0; i < 64; ++i)
+                    if (hg.zm[t] >> i & 1) pt.col[i][t >> 5] |= 1u << (t & 31);
+            }
+            for (int b = 0; b < pt.nbytes; ++b)
+                for (int v = 0; v < 256; ++v)
+                    for (int k = 0; k < 8; ++k) {
+                        const int t = 8 * b + k;
+                        if ((v >> k & 1) && t < hg.nterms) {
+                            pt.tre[b][v] += hg.cre[t];
+                            pt.tim[b][v] += hg.cim[t];
+                        }
+                    }
+            if (cudaMemcpyAsync(dpt, &pt, sizeof pt, cudaMemcpyHostToDevice, st) != cudaSuccess)
+                return cuda_fail("expect upload", err, errlen);
+            const int blog = std::min(12, c.n - 12);
+            nblk = 1 << blog;
+            const int klog = c.n - blog - 8;
+            const size_t dsm = size_t(pt.nbytes) * 256 * 2 * (c.dt == QS_C64 ? sizeof(float) : sizeof(double));
+            static int attr_dev = -1;  // tables of up to 16 bytes x 256 x 2 doubles = 64 KiB
+            int dev = 0;
+            cudaGetDevice(&dev);
+            if (attr_dev != dev) {
+                const int cap = kParityBytes * 256 * 2 * int(sizeof(double));
+                cudaFuncSetAttribute(expect_parity_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
+                cudaFuncSetAttribute(expect_parity_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
+                attr_dev = dev;
+            }
+            if (c.dt == QS_C64)
+                expect_parity_kernel<float><<<nblk, kRedThreads, dsm, st>>>((const float2 *)c.amp, hg.xm, klog, dpt, part);
+            else
+                expect_parity_kernel<double><<<nblk, kRedThreads, dsm, st>>>((const double2 *)c.amp, hg.xm, klog, dpt,
+                                                                             part);
+        } else {
+            if (cudaMemcpyAsync(dgrp, &hg, sizeof(TermGroup), cudaMemcpyHostToDevice, st) != cudaSuccess)
+                return cuda_fail("expect upload", err, errlen);
+            if (c.dt == QS_C64)
+                expect_kernel<float><<<blocks, kRedThreads, 0, st>>>((const float2 *)c.amp, N, dgrp, part);
+            else
+                expect_kernel<double><<<blocks, kRedThreads, 0, st>>>((const double2 *)c.amp, N, dgrp,
+                                                                      part);
+        }
+        finish_kernel<<<1, kRedThreads, 0, st>>>(part, nblk, nblk, res);
         int rc = cuda_fail("expect launch", err, errlen);
         if (rc) return rc;
         double r[2];

@@ -332,3 +332,27 @@ def test_host_fault_injection_paths(monkeypatch):
         assert abs(s.amplitudes()[0] - 1 / math.sqrt(2)) < 1e-6
     finally:
         s.close()
+
+
+@pytest.mark.parametrize("dtype", [qs.QS_C64, qs.QS_C128])
+@pytest.mark.parametrize("n", [16, 19])
+def test_expectation_many_terms_per_x_mask(dtype, n):
+    """Groups of 8..128 Z strings per X mask take the parity-table kernel, larger groups the
+    per-term loop; both against the oracle on a random (circuit-prepared) state."""
+    rng = W.SplitMix64(300 + n)
+    gates = W.layered(n, 3, 77) + W.vqe_circuit(n, 2, 78)
+    want = ref(n, gates)
+    terms = []
+    for xm, count in ((0, 40), (0b101 << 3, 9), (1 << (n - 1), 130), (0b11, 3)):
+        for _ in range(count):
+            zm = rng.next_u64() & ((1 << n) - 1)
+            terms.append((rng.angle() - 3.0, xm, zm))
+    s = qs.State(n, dtype)
+    try:
+        s.apply(gates, qs.options(dtype=dtype))
+        e = s.expect(terms)
+        w = oracle.expect_pauli(want, n, terms)
+        tol = (1e-9 if dtype == qs.QS_C128 else 2e-4) * len(terms)
+        assert abs(e.real - w.real) <= tol and abs(e.imag - w.imag) <= tol
+    finally:
+        s.close()
