@@ -22,13 +22,19 @@ namespace {
 
 constexpr uint32_t kSpinLimit = 1u << 22;
 
-struct __align__(16) BatchShared {
-    uint64_t seg_lo[64], seg_hi[64];
+struct __align__(16) BatchSlot {
+    uint64_t seg_lo[64], seg_hi[64];  // gather tables of the item's pass
     DevPass pass;
     BatchItem item;
     BatchCirc circ;
+    uint64_t base;                    // slab base index in the circuit's state
+    int st;                           // 0 none, 1 ready, 2 dependency wait ran out, 3 not ready yet
+    int pad;
+};
+
+struct __align__(16) BatchShared {
+    BatchSlot slot[2];
     double red[32];
-    int go;
 };
 
 __device__ __forceinline__ unsigned ld_acquire(const unsigned *p)
@@ -38,65 +44,142 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned *p)
     return v;
 }
 
+// Thread 0: take the next item from the queue into slot k.  `block` selects a bounded blocking
+// wait for its dependency (the circuit's previous pass fully stored) or a single check.
+__device__ void take_item(BatchShared &S, int k, const BatchArgs &a)
+{
+    BatchSlot &Z = S.slot[k];
+    const unsigned it = atomicAdd(a.head, 1u);
+    if (it >= a.nitems) {
+        Z.st = 0;
+        return;
+    }
+    Z.item = a.items[it];
+    Z.circ = a.circs[Z.item.circ];
+    Z.pass = a.passes[Z.circ.pass0 + Z.item.pass];
+    Z.st = 1;
+    if (Z.item.pass > 0) {
+        const unsigned need = 1u << Z.circ.nslab_log;
+        if (ld_acquire(a.done + Z.circ.done0 + Z.item.pass - 1) < need) Z.st = 3;
+        __threadfence();
+    }
+}
+
+__device__ void wait_item(BatchShared &S, int k, const BatchArgs &a)
+{
+    BatchSlot &Z = S.slot[k];
+    const unsigned need = 1u << Z.circ.nslab_log;
+    const unsigned *cnt = a.done + Z.circ.done0 + Z.item.pass - 1;
+    uint32_t n = 0;
+    while (ld_acquire(cnt) < need && ++n < kSpinLimit) __nanosleep(128);
+    if (n >= kSpinLimit) {
+        atomicExch(a.status, QS_ETIMEOUT);
+        Z.st = 2;  // skip the work; the host reports the timeout
+    } else {
+        Z.st = 1;
+    }
+    __threadfence();
+}
+
+// All threads: gather tables and slab base of slot k (its item must be known).
+__device__ void prepare_slot(BatchSlot &Z, uint32_t tid, uint32_t nthr)
+{
+    const int lo = Z.pass.lo, nhi = Z.pass.nhi;
+    for (uint32_t j = tid; j < 128; j += nthr) {
+        const uint32_t x = j & 63, sh = (j < 64) ? 0 : 6;
+        uint64_t o = 0;
+        for (int m = 0; m < 6; ++m)
+            if ((x >> m & 1) && int(m + sh) < nhi) o |= 1ull << Z.pass.hipos[m + sh];
+        if (j < 64) Z.seg_lo[x] = o; else Z.seg_hi[x] = o;
+    }
+    if (tid == 0) {
+        uint64_t base = uint64_t(Z.item.slab) << lo;
+        for (int m = 0; m < nhi; ++m) {
+            const uint64_t lowm = (1ull << Z.pass.hipos[m]) - 1;
+            base = ((base & ~lowm) << 1) | (base & lowm);
+        }
+        Z.base = base;
+    }
+}
+
+template <typename C>
+__device__ __forceinline__ uint32_t chunk_of(uint32_t v)
+{
+    return sizeof(C) == 8 ? (swz<1>(v << 1) >> 1) : swz<2>(v);
+}
+
+// All threads: issue the 16-byte gather of slot k's slab into buffer `buf` (passes > 0) and
+// commit one copy group (empty for pass 0, so that every slot owns exactly one group).
+template <typename C>
+__device__ void issue_slot_load(const BatchSlot &Z, C *states, C *buf, uint32_t tid, uint32_t nthr)
+{
+    if (Z.st == 1 && Z.item.pass > 0) {
+        constexpr int kLog16 = (sizeof(C) == 8) ? 1 : 0;
+        const int vps_log = Z.pass.lo - kLog16;
+        const uint32_t nvec = 1u << (Z.pass.b - kLog16);
+        const C *g = states + Z.circ.amp_off + Z.base;
+        const uint32_t dst = smem_addr(buf);
+        for (uint32_t v = tid; v < nvec; v += nthr) {
+            const uint32_t seg = v >> vps_log, w = v & ((1u << vps_log) - 1);
+            const uint64_t so = Z.seg_lo[seg & 63] | Z.seg_hi[(seg >> 6) & 63];
+            cp_async16(dst + 16u * chunk_of<C>(v), reinterpret_cast<const uint4 *>(g + so) + w);
+        }
+    }
+    cp_async_commit();
+}
+
+// Each CTA keeps two items in flight: while item i is computed and stored, the gather of the
+// item taken after it (when its dependency already holds) streams into the other buffer.  An item
+// whose dependency does not hold yet -- for example the next pass of the circuit whose last slab
+// is item i itself -- is waited for only after item i has been stored and counted, so a CTA never
+// waits on its own work.
 template <typename R, int RB, int NT>
 __global__ void __launch_bounds__(NT, 1)
-    batch_kernel(typename Cx<R>::T *__restrict__ states, BatchArgs a)
+    batch_kernel(typename Cx<R>::T *__restrict__ states, BatchArgs a, uint32_t buf_elems)
 {
     using C = typename Cx<R>::T;
     constexpr int SW = sizeof(C) == 8 ? 1 : 2;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     BatchShared &S = *reinterpret_cast<BatchShared *>(smem_raw);
-    C *const sm = reinterpret_cast<C *>(smem_raw + ((sizeof(BatchShared) + 127) & ~size_t(127)));
+    C *const bufs = reinterpret_cast<C *>(smem_raw + ((sizeof(BatchShared) + 127) & ~size_t(127)));
     const uint32_t tid = threadIdx.x;
     const C *coef = reinterpret_cast<const C *>(a.coef);
 
+    int cur = 0;
+    if (tid == 0) {
+        take_item(S, 0, a);
+        if (S.slot[0].st == 3) wait_item(S, 0, a);
+    }
+    __syncthreads();
+    if (S.slot[0].st == 0) return;
+    prepare_slot(S.slot[0], tid, NT);
+    __syncthreads();
+    issue_slot_load<C>(S.slot[0], states, bufs, tid, NT);
+
     while (true) {
-        if (tid == 0) {
-            const unsigned it = atomicAdd(a.head, 1u);
-            S.go = it < a.nitems ? 1 : 0;
-            if (S.go) {
-                S.item = a.items[it];
-                S.circ = a.circs[S.item.circ];
-                S.pass = a.passes[S.circ.pass0 + S.item.pass];
-                if (S.item.pass > 0) {
-                    // wait for every slab of the previous pass of this circuit
-                    const unsigned need = 1u << S.circ.nslab_log;
-                    const unsigned *cnt = a.done + S.circ.done0 + S.item.pass - 1;
-                    uint32_t k = 0;
-                    while (ld_acquire(cnt) < need && ++k < kSpinLimit) __nanosleep(128);
-                    if (k >= kSpinLimit) {
-                        atomicExch(a.status, QS_ETIMEOUT);
-                        S.go = 2;  // skip the work; the host reports the timeout
-                    }
-                    __threadfence();
-                }
-            }
-        }
+        const int nxt = cur ^ 1;
+        BatchSlot &Z = S.slot[cur];
+        BatchSlot &Y = S.slot[nxt];
+        C *const sm = bufs + size_t(cur) * buf_elems;
+        // take the next item; gather it now if its dependency already holds
+        if (tid == 0) take_item(S, nxt, a);
         __syncthreads();
-        const int go = S.go;
-        if (go == 0) break;
-        const int b = S.pass.b, lo = S.pass.lo, nhi = S.pass.nhi;
-        const bool first = S.item.pass == 0, last = S.item.pass == S.circ.npass - 1;
-        for (uint32_t j = tid; j < 128; j += NT) {
-            const uint32_t x = j & 63, sh = (j < 64) ? 0 : 6;
-            uint64_t o = 0;
-            for (int m = 0; m < 6; ++m)
-                if ((x >> m & 1) && int(m + sh) < nhi) o |= 1ull << S.pass.hipos[m + sh];
-            if (j < 64) S.seg_lo[x] = o; else S.seg_hi[x] = o;
+        bool prefetched = false;
+        if (Y.st == 1) {
+            prepare_slot(Y, tid, NT);
+            __syncthreads();
+            issue_slot_load<C>(Y, states, bufs + size_t(nxt) * buf_elems, tid, NT);
+            prefetched = true;
         }
-        uint64_t base = uint64_t(S.item.slab) << lo;
-        for (int m = 0; m < nhi; ++m) {
-            const uint64_t lowm = (1ull << S.pass.hipos[m]) - 1;
-            base = ((base & ~lowm) << 1) | (base & lowm);
-        }
-        C *g = states + S.circ.amp_off + base;
-        const uint32_t nsl = 1u << b;
-        constexpr int kLog16 = (sizeof(C) == 8) ? 1 : 0;
-        const int vps_log = lo - kLog16;
-        const uint32_t nvec = 1u << (b - kLog16);
-        auto chunk_of = [](uint32_t v) -> uint32_t { return sizeof(C) == 8 ? (swz<1>(v << 1) >> 1) : swz<2>(v); };
+        if (prefetched) cp_async_wait<1>();
+        else cp_async_wait<0>();
         __syncthreads();
-        if (go == 1) {
+
+        if (Z.st == 1) {
+            const int b = Z.pass.b, lo = Z.pass.lo, nhi = Z.pass.nhi;
+            const uint64_t base = Z.base;
+            const uint32_t nsl = 1u << b;
+            const bool first = Z.item.pass == 0, last = Z.item.pass == Z.circ.npass - 1;
             if (first) {
                 for (uint32_t i = tid; i < nsl; i += NT) {
                     C z;
@@ -104,18 +187,9 @@ __global__ void __launch_bounds__(NT, 1)
                     z.y = R(0);
                     sm[swz<SW>(i)] = z;
                 }
-            } else {
-                const uint32_t dst = smem_addr(sm);
-                for (uint32_t v = tid; v < nvec; v += NT) {
-                    const uint32_t seg = v >> vps_log, w = v & ((1u << vps_log) - 1);
-                    const uint64_t so = S.seg_lo[seg & 63] | S.seg_hi[(seg >> 6) & 63];
-                    cp_async16(dst + 16u * chunk_of(v), reinterpret_cast<const uint4 *>(g + so) + w);
-                }
-                cp_async_commit();
-                cp_async_wait<0>();
+                __syncthreads();
             }
-            __syncthreads();
-            for (int o = S.pass.op_begin; o < S.pass.op_end; ++o) {
+            for (int o = Z.pass.op_begin; o < Z.pass.op_end; ++o) {
                 const DevOp &op = a.ops[o];
                 if ((base & op.ocmask) == op.ocmask) {
                     if (op.type == OP_STAGE) run_stage<C, RB>(sm, a.stages + op.mat, a.subs, coef, base, tid, NT);
@@ -128,11 +202,11 @@ __global__ void __launch_bounds__(NT, 1)
                 double acc = 0.0;
                 R part = 0;
                 int cnt = 0;
-                const BatchTerm *T = a.terms + S.circ.term0;
-                const int nt = S.circ.nterm;
+                const BatchTerm *T = a.terms + Z.circ.term0;
+                const int nt = Z.circ.nterm;
                 for (uint32_t i = tid; i < nsl; i += NT) {
                     uint64_t x = base | (i & ((1u << lo) - 1));
-                    for (int m = 0; m < nhi; ++m) x |= uint64_t((i >> (lo + m)) & 1u) << S.pass.hipos[m];
+                    for (int m = 0; m < nhi; ++m) x |= uint64_t((i >> (lo + m)) & 1u) << Z.pass.hipos[m];
                     R h = 0;
                     for (int t = 0; t < nt; ++t) h += (__popcll(x & T[t].zm) & 1) ? -R(T[t].c) : R(T[t].c);
                     const C v = sm[swz<SW>(i)];
@@ -153,26 +227,41 @@ __global__ void __launch_bounds__(NT, 1)
                     double v = tid < NT / 32 ? S.red[tid] : 0.0;
 #pragma unroll
                     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-                    if (tid == 0) atomicAdd(a.results + S.item.circ, v);
+                    if (tid == 0) atomicAdd(a.results + Z.item.circ, v);
                 }
             }
+            constexpr int kLog16 = (sizeof(C) == 8) ? 1 : 0;
+            const int vps_log = lo - kLog16;
+            const uint32_t nvec = 1u << (b - kLog16);
+            C *g = states + Z.circ.amp_off + base;
             for (uint32_t v = tid; v < nvec; v += NT) {
                 const uint32_t seg = v >> vps_log, w = v & ((1u << vps_log) - 1);
-                const uint64_t so = S.seg_lo[seg & 63] | S.seg_hi[(seg >> 6) & 63];
-                st_stream(reinterpret_cast<uint4 *>(g + so) + w, reinterpret_cast<const uint4 *>(sm)[chunk_of(v)]);
+                const uint64_t so = Z.seg_lo[seg & 63] | Z.seg_hi[(seg >> 6) & 63];
+                st_stream(reinterpret_cast<uint4 *>(g + so) + w, reinterpret_cast<const uint4 *>(sm)[chunk_of<C>(v)]);
             }
         }
         __threadfence();
         __syncthreads();
-        if (tid == 0) atomicAdd(a.done + S.circ.done0 + S.item.pass, 1u);
+        if (tid == 0) atomicAdd(a.done + Z.circ.done0 + Z.item.pass, 1u);
+        // the next item: stop, or wait for its dependency now that this item is counted
+        if (Y.st == 0) break;
+        if (Y.st == 3) {
+            if (tid == 0) wait_item(S, nxt, a);
+            __syncthreads();
+            prepare_slot(Y, tid, NT);
+            __syncthreads();
+            issue_slot_load<C>(Y, states, bufs + size_t(nxt) * buf_elems, tid, NT);
+        }
+        cur = nxt;
     }
+    cp_async_wait<0>();
 }
 
 template <typename R, int RB, int NT>
 int launch_batch_t(void *states, const BatchArgs &a, int b_max, void *stream, char *err, size_t errlen)
 {
     using C = typename Cx<R>::T;
-    const size_t smem = ((sizeof(BatchShared) + 127) & ~size_t(127)) + (sizeof(C) << b_max);
+    const size_t smem = ((sizeof(BatchShared) + 127) & ~size_t(127)) + 2 * (sizeof(C) << b_max);
     static int attr_dev = -1;
     int dev = 0;
     cudaGetDevice(&dev);
@@ -182,7 +271,12 @@ int launch_batch_t(void *states, const BatchArgs &a, int b_max, void *stream, ch
     }
     unsigned grid = (unsigned)num_sms();
     if (grid > a.nitems) grid = a.nitems > 0 ? a.nitems : 1;
-    batch_kernel<R, RB, NT><<<grid, NT, smem, (cudaStream_t)stream>>>(reinterpret_cast<C *>(states), a);
+    if (smem > 227 * 1024) {
+        snprintf(err, errlen, "batch slab of %d bits does not fit two buffers in shared memory", b_max);
+        return QS_EINVAL;
+    }
+    batch_kernel<R, RB, NT><<<grid, NT, smem, (cudaStream_t)stream>>>(reinterpret_cast<C *>(states), a,
+                                                                       uint32_t(1) << b_max);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
         snprintf(err, errlen, "batch launch failed: %s", cudaGetErrorString(e));
