@@ -16,7 +16,7 @@ struct LearnedMeta {
 };
 
 // Build the greedy plan for `opt` into `greedy`; with a model, also score the candidate grid
-// and, when one is predicted >= 2% faster, move it into `best` (meta.chosen >= 0).
+// and, when one is predicted >= 5% faster, move it into `best` (meta.chosen >= 0).
 int learned_choose(const std::vector<CGate> &gates, int n, qs_dtype dt, const qs_options &opt, qs_model *model,
                    Plan &greedy, Plan &best, LearnedMeta &meta, std::string &err);
 

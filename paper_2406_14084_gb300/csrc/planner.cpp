@@ -600,8 +600,12 @@ bool controlled_phase(const CGate &g, cd &phase)
 // fewest positions meeting every interval are found by the greedy interval-stabbing rule
 // (sort by right end, place a point at the first uncovered right end).  Each group of two or
 // more diagonals whose element-wise product is cheaper as one table (one complex multiply per
-// amplitude) than as separate subs becomes one SB_DIAG with no outer bits.  Diagonals that
-// read bits outside the registers stay where they are.
+// amplitude) than as separate subs becomes one SB_DIAG.  A controlled phase whose condition
+// includes slab bits outside the registers or physical bits outside the slab joins too: those
+// bits are constant for a thread's group, so they index the table (up to kMergeCondBits of them
+// per table).  Diagonal tables that already read such bits stay where they are.
+constexpr int kMergeCondBits = 6;  // condition bits of one merged table (2^(RB + 6) entries at most)
+
 void merge_stage_diagonals(Plan &plan, int s0, int RB, Coefs &cf)
 {
     const int E = 1 << RB;
@@ -616,9 +620,11 @@ void merge_stage_diagonals(Plan &plan, int s0, int RB, Coefs &cf)
     };
     auto is_diag = [](const DevSub &s) { return s.type == SB_PHASE || s.type == SB_DIAG; };
     auto eligible = [](const DevSub &s) {
-        return (s.type == SB_PHASE && s.lcm == 0 && s.ocm == 0) || (s.type == SB_DIAG && s.ndl == 0);
+        return (s.type == SB_PHASE && __builtin_popcount(s.lcm) + __builtin_popcountll(s.ocm) <= kMergeCondBits) ||
+               (s.type == SB_DIAG && s.ndl == 0);
     };
     std::vector<std::vector<cd>> tab(ns);
+    std::vector<std::vector<uint8_t>> cond(ns);  // bits (DevSub::dl codes) that must all be 1
     std::vector<uint32_t> reads(ns, 0);
     std::vector<double> cost(ns, 0.0);
     std::vector<int> slot(ns, 0), nd_index;  // nd_index: positions of non-diagonal subs
@@ -634,7 +640,11 @@ void merge_stage_diagonals(Plan &plan, int s0, int RB, Coefs &cf)
             const cd p = plan.coef[in[i].mat];
             for (int e = 0; e < E; ++e)
                 if ((uint32_t(e) & in[i].scm) == in[i].scm) t[e] = p;
-            const double frac = std::ldexp(1.0, -__builtin_popcount(in[i].scm));
+            for (int l = 0; l < 32; ++l)
+                if (in[i].lcm >> l & 1) cond[i].push_back((uint8_t)l);
+            for (int q = 0; q < 64; ++q)
+                if (in[i].ocm >> q & 1) cond[i].push_back((uint8_t)(0x80 | q));
+            const double frac = std::ldexp(1.0, -__builtin_popcount(in[i].scm) - (int)cond[i].size());
             cost[i] = E * frac * (p == cd(-1.0) ? 0.25 : 1.0);
         } else {
             for (int e = 0; e < E; ++e) t[e] = plan.coef[in[i].mat + e];
@@ -665,17 +675,25 @@ void merge_stage_diagonals(Plan &plan, int s0, int RB, Coefs &cf)
     std::sort(cand.begin(), cand.end(), [&](int a, int b) { return hi[a] < hi[b] || (hi[a] == hi[b] && a < b); });
     std::vector<int> point(ns, -1);
     std::vector<std::vector<int>> groups;
+    std::vector<std::vector<uint8_t>> gcond;  // union of the members' condition bits
     std::vector<int> gpoint;
     for (int i : cand) {
         if (point[i] >= 0) continue;
         const int p = hi[i];
         std::vector<int> gr;
-        for (int j : cand)
-            if (point[j] < 0 && lo[j] <= p && p <= hi[j]) {
-                point[j] = p;
-                gr.push_back(j);
-            }
+        std::vector<uint8_t> un;
+        for (int j : cand) {
+            if (point[j] >= 0 || lo[j] > p || p > hi[j]) continue;
+            std::vector<uint8_t> u2 = un;
+            for (uint8_t c : cond[j])
+                if (std::find(u2.begin(), u2.end(), c) == u2.end()) u2.push_back(c);
+            if ((int)u2.size() > kMergeCondBits) continue;  // left for another table
+            un = std::move(u2);
+            point[j] = p;
+            gr.push_back(j);
+        }
         groups.push_back(gr);
+        gcond.push_back(un);
         gpoint.push_back(p);
     }
     std::vector<char> merged(ns, 0);
@@ -686,15 +704,24 @@ void merge_stage_diagonals(Plan &plan, int s0, int RB, Coefs &cf)
         double c = 0;
         for (int i : gr) c += cost[i];
         if (gr.size() < 2 || c <= 1.25 * E) continue;
-        std::vector<cd> t(E, cd(1.0));
+        // table over (condition bits hi, register index e): a member contributes where all of its
+        // condition bits are set in hi
+        const std::vector<uint8_t> &un = gcond[gi];
+        const int ndl = (int)un.size();
+        std::vector<cd> t(size_t(E) << ndl, cd(1.0));
         for (int i : gr) {
-            for (int e = 0; e < E; ++e) t[e] *= tab[i][e];
+            uint32_t need = 0;
+            for (uint8_t cbit : cond[i]) need |= 1u << (std::find(un.begin(), un.end(), cbit) - un.begin());
+            for (uint32_t h = 0; h < (1u << ndl); ++h)
+                if ((h & need) == need)
+                    for (int e = 0; e < E; ++e) t[(size_t(h) << RB) | e] *= tab[i][e];
             merged[i] = 1;
         }
         DevSub s;
         std::memset(&s, 0, sizeof s);
         s.type = SB_DIAG;
-        s.ndl = 0;
+        s.ndl = (uint8_t)ndl;
+        for (int j = 0; j < ndl; ++j) s.dl[j] = un[j];
         s.mat = cf.push(t);
         at[gpoint[gi]].push_back(s);
         changed = true;
