@@ -80,6 +80,7 @@ def lib():
             L.or_norm2.argtypes = [dp, ctypes.c_int]
             L.or_norm2.restype = ctypes.c_double
             L.or_probs.argtypes = [dp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int, dp]
+            L.or_sample.argtypes = [dp, ctypes.c_int, dp, ctypes.c_int64, ctypes.c_void_p]
             u64p = ctypes.POINTER(ctypes.c_uint64)
             L.or_expect_pauli.argtypes = [dp, ctypes.c_int, dp, u64p, u64p, ctypes.c_int, dp]
             L.or_circuit_unitary.argtypes = [ctypes.POINTER(_Gate), ctypes.c_int, ctypes.c_int, dp]
@@ -188,6 +189,17 @@ def probs(state: np.ndarray, n: int, qubits) -> np.ndarray:
     rc = lib().or_probs(_dptr(state), n, q, nq, _dptr(out))
     if rc:
         raise ValueError("bad probs request")
+    return out
+
+
+def sample(state: np.ndarray, n: int, u) -> np.ndarray:
+    """Outcome per uniform u[k] in [0, 1): smallest x whose running sum of |a_y|^2 (y <= x)
+    exceeds u[k] times the total (inverse transform sampling of the Born distribution)."""
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    out = np.empty(u.size, dtype=np.uint64)
+    rc = lib().or_sample(_dptr(state), n, _dptr(u), u.size, out.ctypes.data_as(ctypes.c_void_p))
+    if rc:
+        raise ValueError("bad sample request")
     return out
 
 

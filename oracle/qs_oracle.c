@@ -331,6 +331,40 @@ double or_norm2(const double *state, int n)
 }
 
 /* Marginal probabilities: out[m] = sum of |a_x|^2 over x whose qubit q[j] equals bit j of m. */
+/* Measurement sampling in the computational basis (Born rule, Eq. 1: outcome x has
+ * probability |a_x|^2 / sum_y |a_y|^2).  For each caller-supplied uniform u[k] in [0, 1), the
+ * outcome is the smallest x with C(x) > u[k] * C(2^n - 1), where C(x) = sum_{y <= x} |a_y|^2 is
+ * the running sum taken in index order (inverse transform sampling).  Plain sequential FP64. */
+int or_sample(const double *state, int n, const double *u, int64_t shots, uint64_t *out)
+{
+    const cplx *a = (const cplx *)state;
+    const int64_t N = (int64_t)1 << n;
+    double *cdf = (double *)malloc(sizeof(double) * (size_t)N);
+    if (!cdf) return -2;
+    double run = 0.0;
+    for (int64_t x = 0; x < N; ++x) {
+        const double re = creal(a[x]), im = cimag(a[x]);
+        run += re * re + im * im;
+        cdf[x] = run;
+    }
+    for (int64_t k = 0; k < shots; ++k) {
+        if (!(u[k] >= 0.0 && u[k] < 1.0)) {
+            free(cdf);
+            return -1;
+        }
+        const double t = u[k] * run;
+        int64_t lo = 0, hi = N - 1; /* smallest x with cdf[x] > t */
+        while (lo < hi) {
+            const int64_t mid = lo + (hi - lo) / 2;
+            if (cdf[mid] > t) hi = mid;
+            else lo = mid + 1;
+        }
+        out[k] = (uint64_t)lo;
+    }
+    free(cdf);
+    return 0;
+}
+
 int or_probs(const double *state, int n, const int *q, int nq, double *out)
 {
     const cplx *a = (const cplx *)state;

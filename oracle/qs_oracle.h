@@ -54,6 +54,7 @@ void or_init_basis(double *state, int n, uint64_t x);
 int or_remap(double *state, int n, int k, const int *A, const int *B);
 double or_norm2(const double *state, int n);
 int or_probs(const double *state, int n, const int *q, int nq, double *out);
+int or_sample(const double *state, int n, const double *u, int64_t shots, uint64_t *out);
 int or_expect_pauli(const double *state, int n, const double *coeff, const uint64_t *xmask,
                     const uint64_t *zmask, int nterms, double *out);
 int or_circuit_unitary(const or_gate *gates, int ng, int k, double *U);

@@ -471,3 +471,34 @@ def test_adam_first_step_moves_by_lr_times_sign():
     v = np.zeros(3)
     oracle.adam_step(p, g, m, v, 1, lr=0.01, eps=1e-12)
     assert np.allclose(p, [1.0 - 0.01, -2.0 + 0.01, 3.0 - 0.01], atol=1e-9)
+
+
+def test_sampling_inverse_transform_pins():
+    """Born-rule sampling by inverse transform: closed forms that fix the index order, the
+    strict inequality at CDF steps, and the normalisation by the total weight."""
+    n = 5
+    # basis state: every draw lands on it
+    a = oracle.basis_state(n, 19)
+    assert np.all(oracle.sample(a, n, [0.0, 0.3, 0.999999]) == 19)
+    # H on all qubits: uniform, outcome = floor(u * 2^n)
+    a = oracle.apply_circuit(n, [Gate("H", (q,)) for q in range(n)])
+    u = np.array([0.0, 0.01, 0.5, 0.77, 0.999])
+    assert np.array_equal(oracle.sample(a, n, u), np.floor(u * 32).astype(np.uint64))
+    # RY(theta) on qubit 2 only: P(x = 4) = sin^2(theta / 2), outcomes 0 and 4
+    th = 1.1
+    a = oracle.apply_circuit(n, [Gate("RY", (2,), (), (th,))])
+    p0 = math.cos(th / 2) ** 2
+    got = oracle.sample(a, n, [p0 - 1e-9, p0 + 1e-9, 0.0])
+    assert list(got) == [0, 4, 0]
+    # unnormalised input: the total weight rescales u
+    b = 3.0 * a
+    assert list(oracle.sample(b, n, [p0 - 1e-9, p0 + 1e-9])) == [0, 4]
+    # brute force against sorted cumulative weights on a random state
+    a = oracle.apply_circuit(6, W.random_circuit(6, 40, 12))
+    w = np.abs(a) ** 2
+    cdf = np.cumsum(w)
+    u = np.random.default_rng(3).random(200)
+    want = np.searchsorted(cdf, u * cdf[-1], side="right")
+    assert np.array_equal(oracle.sample(a, 6, u), want.astype(np.uint64))
+    with pytest.raises(ValueError):
+        oracle.sample(a, 6, [1.0])
