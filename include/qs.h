@@ -256,6 +256,14 @@ qs_status qs_probs(qs_state *s, const int *qubits, int nq, double *host_out);
 qs_status qs_probs_noalloc(const void *dev_amp, int n, qs_dtype dt, const int *qubits, int nq,
                            void *stream, double *host_out);
 
+/* Measurement sampling in the computational basis (Born rule: outcome x with probability
+ * |a_x|^2 / ||psi||^2, Eq. 1).  For each caller-supplied uniform u[k] in [0, 1) (the caller's
+ * random numbers; the library draws none), host_out[k] receives the smallest logical index x
+ * whose running weight sum_{y <= x} |a_y|^2 exceeds u[k] ||psi||^2 (inverse transform sampling,
+ * in logical qubit order).  shots <= 2^28.  QS_EINVAL for a u outside [0, 1) or a zero state.
+ * Synchronises; one read of the state plus one 2^12-amplitude block per shot. */
+qs_status qs_sample(qs_state *s, const double *u, size_t shots, uint64_t *host_out);
+
 /* host_out[0] = Re sum_t coeff_t <psi|P_t|psi>, host_out[1] = its imaginary part (zero up to
  * rounding for Hermitian sums).  FP64 accumulation.  Synchronises. */
 qs_status qs_expect_pauli_sum(qs_state *s, const qs_pauli_term *terms, size_t nterms,

@@ -938,6 +938,44 @@ qs_status qs_norm2(qs_state *s, double *host_out)
     QS_GUARD_END
 }
 
+qs_status qs_sample(qs_state *s, const double *u, size_t shots, uint64_t *host_out)
+{
+    QS_GUARD_BEGIN
+    if (!s || (shots && (!u || !host_out))) return fail(QS_EINVAL, "NULL argument");
+    if (shots > (size_t(1) << 28)) return fail(QS_EINVAL, "at most 2^28 shots per call");
+    for (size_t k = 0; k < shots; ++k)
+        if (!(u[k] >= 0.0 && u[k] < 1.0)) return fail(QS_EINVAL, "uniforms must lie in [0, 1)");
+    qs_status st = canonicalize_state(s);  // outcomes are logical indices
+    if (st) return st;
+    const size_t base = (sample_scratch_bytes(s->n) + 255) & ~size_t(255);
+    st = ensure_scratch(s, base + shots * (sizeof(double) + sizeof(uint64_t)) + 256);
+    if (st) return st;
+    char *scr = reinterpret_cast<char *>(s->scratch);
+    double *d_u = reinterpret_cast<double *>(scr + base);
+    uint64_t *d_out = reinterpret_cast<uint64_t *>(scr + base + shots * sizeof(double));
+    if (shots) {
+        st = cuda_status(cudaMemcpyAsync(d_u, u, shots * sizeof(double), cudaMemcpyHostToDevice, s->stream),
+                         "sample upload");
+        if (st) return st;
+    }
+    LaunchCtx c{s->amp, s->n, s->dt, (void *)s->stream};
+    char err[256] = {0};
+    const int rc = launch_sample(c, d_u, shots, d_out, s->scratch, err, sizeof err);
+    if (rc) return fail((qs_status)rc, err);
+    double total = 0.0;
+    st = cuda_status(cudaMemcpyAsync(&total, s->scratch + sample_total_index(s->n), sizeof(double),
+                                     cudaMemcpyDeviceToHost, s->stream),
+                     "sample readback");
+    if (!st && shots)
+        st = cuda_status(cudaMemcpyAsync(host_out, d_out, shots * sizeof(uint64_t), cudaMemcpyDeviceToHost, s->stream),
+                         "sample readback");
+    if (!st) st = cuda_status(cudaStreamSynchronize(s->stream), "sample");
+    if (st) return st;
+    if (!(total > 0.0)) return fail(QS_EINVAL, "the state has zero norm");
+    return QS_OK;
+    QS_GUARD_END
+}
+
 qs_status qs_probs(qs_state *s, const int *qubits, int nq, double *host_out)
 {
     QS_GUARD_BEGIN

@@ -202,6 +202,13 @@ int launch_expect(const LaunchCtx &c, const uint64_t *xm, const uint64_t *zm,
                   double *h_out, char *err, size_t errlen);
 int launch_set_basis(const LaunchCtx &c, uint64_t x, char *err, size_t errlen);
 
+// Measurement sampling (k_sample.cu): d_out[k] = outcome of uniform d_u[k]; the scratch must
+// hold sample_scratch_bytes(n); the total weight is left at double index sample_total_index(n).
+size_t sample_scratch_bytes(int n);
+size_t sample_total_index(int n);
+int launch_sample(const LaunchCtx &c, const double *d_u, uint64_t shots, uint64_t *d_out, void *d_scratch,
+                  char *err, size_t errlen);
+
 // Marginal probabilities with a fixed file-scope device histogram instead of allocated scratch
 // (qs_probs_noalloc).  nq <= kStaticProbsMaxQubits.
 constexpr int kStaticProbsMaxQubits = 14;

@@ -132,6 +132,7 @@ _SIGS = {
     "qs_probs": [_vp, ctypes.POINTER(_i), _i, _dp],
     "qs_probs_noalloc": [_vp, _i, _i, ctypes.POINTER(_i), _i, _vp, _dp],
     "qs_expect_pauli_sum": [_vp, ctypes.POINTER(QsPauliTerm), ctypes.c_size_t, _dp],
+    "qs_sample": [_vp, _dp, ctypes.c_size_t, ctypes.c_void_p],
     "qs_stats": [_vp, ctypes.POINTER(QsStats)],
     "qs_stats_reset": [_vp],
     "qs_set_profiling": [_vp, _i],
@@ -483,6 +484,14 @@ def qs_probs_noalloc(dev_ptr: int, n: int, dtype: int, qubits, stream: int = 0,
     return out
 
 
+def qs_sample(state, u) -> np.ndarray:
+    """Outcome (logical index) for each uniform u[k] in [0, 1)."""
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    out = np.zeros(u.size, dtype=np.uint64)
+    _check(lib().qs_sample(state, u.ctypes.data_as(_dp), u.size, out.ctypes.data_as(_vp)))
+    return out
+
+
 def qs_expect_pauli_sum(state, terms) -> complex:
     nt = len(terms)
     arr = (QsPauliTerm * max(1, nt))()
@@ -599,6 +608,9 @@ class State:
 
     def expect(self, terms):
         return qs_expect_pauli_sum(self.h, terms)
+
+    def sample(self, u):
+        return qs_sample(self.h, u)
 
     def norm2(self):
         return qs_norm2(self.h)
