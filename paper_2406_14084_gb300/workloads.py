@@ -172,6 +172,21 @@ def qaoa_like(n: int, p: int, seed: int):
     return gates
 
 
+def qaoa_complete(n: int, p: int, seed: int):
+    """QAOA on the complete graph: H on all; p rounds of RZZ on every pair (i < j) and RX on all.
+    n + p (n (n - 1) / 2 + n) gates: 2,511 for n = 31, p = 5 (the paper's QAOA size)."""
+    rng = SplitMix64(seed)
+    gates = [Gate("H", (q,)) for q in range(n)]
+    for _ in range(p):
+        gamma, beta = rng.angle(), rng.angle()
+        for i in range(n):
+            for j in range(i + 1, n):
+                gates.append(Gate("RZZ", (i, j), (), (gamma,)))
+        for q in range(n):
+            gates.append(Gate("RX", (q,), (), (beta,)))
+    return gates
+
+
 def gate_sweep(n: int, kind: str, reps: int, seed: int):
     """``kind`` applied to every qubit ``reps`` times (two-qubit kinds on (q, q+1 mod n))."""
     rng = SplitMix64(seed)
