@@ -105,9 +105,8 @@ typedef struct {
                             cost model says the wider gate costs more (a learned-planner
                             candidate); 0 = merge only where the model says it pays */
     int32_t euler;       /* blocked plans: write complex 1-qubit gates as phase, real rotation,
-                            phase (Z-Y-Z) so that register stages merge the phases.  0 = auto
-                            (complex128 only, whose FP64 pipe bounds the pass), 1 = never,
-                            2 = always */
+                            phase (Z-Y-Z) so that register stages merge the phases.  0 or 2 =
+                            split (the default), 1 = keep complex 2x2 matrices */
     int32_t reserved[2];
 } qs_options;
 

@@ -1266,7 +1266,7 @@ int build_plan(const std::vector<CGate> &gates_in, int n, qs_dtype dt, const qs_
         gates = fuse_pass(gates, kdiag, kTcTargets, true, false, dt);
         for (const CGate &g : gates) is_tc.push_back(g.cls == C_DENSE && g.tq.size() >= 4);
     } else if (opt.fuse_width > 0) {
-        const bool euler = opt.euler == 2 || (opt.euler == 0 && dt == QS_C128);
+        const bool euler = opt.euler != 1;
         if (opt.blocking && euler) gates = split_one_qubit(gates);
         const int kdiag = opt.diag_bits > 0 ? std::min(opt.diag_bits, kMaxDiagBits) : 10;
         int kdense = std::min(opt.fuse_width, kMaxDense);

@@ -263,7 +263,7 @@ def test_euler_split_of_generic_unitaries_and_rz():
         check_plan(gates, n, qs.options(slab_bits=7, seg_bits=2, dtype=dtype, euler=2), seed=4)
 
 
-def test_euler_default_follows_precision():
+def test_euler_split_is_the_default_and_can_be_turned_off():
     g = W.layered(12, 4, 7)
     counts = {}
     for dtype in (qs.QS_C64, qs.QS_C128):
@@ -271,5 +271,5 @@ def test_euler_default_follows_precision():
             p = qs.qs_fuse(g, 12, qs.options(dtype=dtype, euler=eu, slab_bits=9, seg_bits=3))
             counts[dtype, eu] = qs.qs_plan_features(p)[:, 17].sum()  # real 1-qubit rotations
             qs.qs_plan_destroy(p)
-    assert counts[qs.QS_C64, 0] == counts[qs.QS_C64, 1] == 0
-    assert counts[qs.QS_C128, 0] == counts[qs.QS_C128, 2] > 0 and counts[qs.QS_C128, 1] == 0
+    for dtype in (qs.QS_C64, qs.QS_C128):
+        assert counts[dtype, 0] == counts[dtype, 2] > 0 and counts[dtype, 1] == 0
