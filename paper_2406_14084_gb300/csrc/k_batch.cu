@@ -3,10 +3,12 @@
 // The host concatenates the slab-pass plans of all circuits and lists work items (circuit,
 // pass, slab) in dependency rounds: every circuit's pass 0, then every pass 1, and so on.
 // Persistent CTAs take items from an atomic queue head in that order.  Before pass p > 0 of a
-// circuit may start, all slabs of its pass p-1 must be stored: thread 0 spins, with a bounded
-// number of polls, on the circuit's done counter for pass p-1 (acquire loads; producers
-// release with a fence before incrementing).  Items are handed out in order and a CTA never
-// waits on an item handed out after its own, so the earliest unfinished item can always run.
+// circuit may start, all slabs of its pass p-1 must be stored (the circuit's done counter for
+// pass p-1, read with acquire loads; producers release with a fence before incrementing).
+// Each CTA keeps two items: while one is computed, the next one's gather streams into the
+// second buffer if its dependency already holds; otherwise thread 0 waits for it (a bounded
+// number of polls) only after the current item has been stored and counted.  So a CTA never
+// waits on its own work, and the earliest unfinished item in queue order can always run.
 // Pass 0 initialises |0..0> in shared memory instead of loading the state; the last pass
 // accumulates the circuit's Z-string expectation sum_x |a_x|^2 h(x) from the slab in shared
 // memory (FP32 partial sums of at most 32 amplitudes, then FP64) and adds it to the

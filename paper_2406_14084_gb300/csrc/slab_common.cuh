@@ -12,75 +12,17 @@ namespace qs {
 
 namespace {
 
-constexpr uint32_t kWaitLimit = 1u << 24;  // mbarrier polls (with backoff) before giving up
-
 struct __align__(16) SlabShared {
     uint64_t seg_lo[64];   // deposit of hi-bit index bits 0..5 into physical positions
     uint64_t seg_hi[64];   // deposit of hi-bit index bits 6..11
     uint16_t inv_lo[256];  // store permutation: source local index of destination bits 0..7
     uint16_t inv_hi[256];  //                                    ... of destination bits 8..15
     DevPass pass;
-    unsigned long long full[2];   // TMA load of buffer k has landed
-    unsigned long long empty[2];  // buffer k has been stored back and may be refilled
 };
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p)
 {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
-{
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity)
-{
-    for (uint32_t i = 0; i < kWaitLimit; ++i) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if (i > 64) __nanosleep(128);
-    }
-    return false;
-}
-
-// 1-D bulk copy global -> shared (TMA), completion counted on the mbarrier in bytes.
-__device__ __forceinline__ void tma_load_1d(uint32_t dst, const void *src, uint32_t bytes,
-                                            uint32_t bar)
-{
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            dst),
-        "l"(src), "r"(bytes), "r"(bar)
-        : "memory");
-}
-
-__device__ __forceinline__ void fence_proxy_async()
-{
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-__device__ __forceinline__ void fence_mbar_init()
-{
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
 __device__ __forceinline__ void st_stream(uint4 *p, uint4 v)
@@ -429,32 +371,6 @@ __device__ __noinline__ void run_smem_op(C *sm, int b, const DevOp &op, const C 
     if (op.type == OP_DIAG)
         for (int j = 0; j < op.nout; ++j) toff |= uint32_t((base >> op.outpos[j]) & 1) << (op.k + j);
     apply_op<C, uint32_t, (sizeof(C) == 8 ? 1 : 2)>(sm, b, op, coef, toff, tid, nthr);
-}
-
-// Named barrier 1 among the NT compute threads (the producer warp never joins it).
-__device__ __forceinline__ void compute_sync(uint32_t nthreads)
-{
-    asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory");
-}
-
-// OR of a predicate over the NT compute threads (also a barrier).
-__device__ __forceinline__ bool compute_any(bool v, uint32_t nthreads)
-{
-    uint32_t r;
-    asm volatile(
-        "{\n\t.reg .pred p, q;\n\t"
-        "setp.ne.u32 p, %1, 0;\n\t"
-        "bar.red.or.pred q, 1, %2, p;\n\t"
-        "selp.u32 %0, 1, 0, q;\n\t}"
-        : "=r"(r)
-        : "r"(uint32_t(v)), "r"(nthreads)
-        : "memory");
-    return r != 0;
-}
-
-__device__ __forceinline__ void mbar_arrive(uint32_t bar)
-{
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
 // 16-byte asynchronous global -> shared copies (L2 only, no L1 allocation).
