@@ -46,6 +46,8 @@ WORKLOADS = {
     "config1": dict(n=20, dtype="c128", kind="random", ngates=200, seed=1001),
     "batch1024_c64": dict(n=24, dtype="c64", kind="batch", count=1024, seed=1004),
     "batch1024_c128": dict(n=24, dtype="c128", kind="batch", count=1024, seed=1004),
+    "batch64_c64": dict(n=20, dtype="c64", kind="batch", count=64, seed=1004, nmax=20),
+    "readout28_c64": dict(n=28, dtype="c64", kind="readout", seed=1009),
     "qaoa31_c128": dict(n=31, dtype="c128", kind="qaoa", p=5, seed=1006),
     "qft31_c128": dict(n=31, dtype="c128", kind="qft", seed=1006),
     "gatesweep30_c128": dict(n=30, dtype="c128", kind="gatesweep", reps=2, seed=1007),
@@ -248,7 +250,7 @@ def oracle_sample_batch(w, budget_s: float):
     import oracle
     from paper_2406_14084_gb300 import workloads as W
 
-    circuits = W.vqe_batch(w["count"], w["seed"])
+    circuits = W.vqe_batch(w["count"], w["seed"], nmax=w.get("nmax", 24))
     total_gates = sum(len(g) for _, g in circuits)
     total_work = sum(len(g) * (1 << n) for n, g in circuits)
     done_work, done_c, t0 = 0, 0, time.perf_counter()
@@ -276,7 +278,7 @@ def run_batch(args, w):
 
     torch.cuda.set_device(0)
     dtype = qs.QS_C64 if w["dtype"] == "c64" else qs.QS_C128
-    circuits = W.vqe_batch(w["count"], w["seed"])
+    circuits = W.vqe_batch(w["count"], w["seed"], nmax=w.get("nmax", 24))
     H = W.zz_chain_hamiltonian(24)
     ngates = sum(len(g) for _, g in circuits)
     t_plan0 = time.perf_counter()
@@ -394,6 +396,55 @@ def run_learned(args, w):
         "gain_vs_greedy": ms["greedy"] / ms["learned"], "circuits": rows, "clocks": clk,
         "gpu_launches": launches,
     }
+
+def run_readouts(args, w):
+    """The readout step (norm, marginal probabilities, Pauli-sum expectation, sampling) on an
+    n-qubit state: each is one read of the state, so the roofline is 2^n * s bytes per call over
+    its wall time (each call synchronises and returns host data)."""
+    import numpy as np
+    import torch
+
+    from paper_2406_14084_gb300 import qs
+    from paper_2406_14084_gb300 import workloads as W
+
+    torch.cuda.set_device(0)
+    dtype = qs.QS_C64 if w["dtype"] == "c64" else qs.QS_C128
+    n = w["n"]
+    s_amp = 8 if dtype == qs.QS_C64 else 16
+    H = W.zz_chain_hamiltonian(n)
+    u = np.random.default_rng(w["seed"]).random(100000)
+    calls = {"norm2": lambda st: st.norm2(), "probs_3q": lambda st: st.probs([0, n // 2, n - 1]),
+             "expect_zz_chain": lambda st: st.expect(H), "sample_100k": lambda st: st.sample(u)}
+    rows = {}
+    peaks = measured_peaks()
+    clocks = ClockSampler(0)
+    with qs.State(n, dtype) as st:
+        st.apply(W.layered(n, 2, w["seed"]), qs.options(dtype=dtype))
+        clocks.start()
+        for name, f in calls.items():
+            for _ in range(args.warmup):
+                f(st)
+            ts = []
+            for _ in range(args.steps):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                f(st)
+                ts.append(time.perf_counter() - t0)
+            best = min(ts)
+            gbs = (1 << n) * s_amp / best / 1e9
+            rows[name] = {"ms": 1e3 * best, "gbs": gbs, "frac_of_hbm": gbs / peaks["hbm_gbs"]}
+        clk = clocks.stop()
+    ms_total = sum(r["ms"] for r in rows.values())
+    return {
+        "metric": "readouts/s", "value": len(rows) / (ms_total / 1e3), "unit": "readouts/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_total, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": w["dtype"], "data": "synthetic (seeded layered state)",
+        "config": {"workload": args.workload, "qubits": n, "terms": len(H), "shots": int(u.size),
+                   "l2": "state larger than L2"},
+        "readouts": rows, "hbm_peak_gbs": peaks["hbm_gbs"], "peak_source": peaks["source"], "clocks": clk,
+        "gpu_launches": None,
+    }
+
 
 TABLE1_KINDS = ["H", "X", "Y", "Z", "S", "T", "RX", "RY", "RZ", "U3", "CX", "CZ", "CP", "SWAP", "RZZ"]
 
@@ -744,11 +795,15 @@ def main():
         if rank != 0:
             return
         line = run_gate_sweeps(args, w)
+    elif w["kind"] == "readout":
+        if rank != 0:
+            return
+        line = run_readouts(args, w)
     else:
         line = run_gpu(args, w, ws, rank, local)
     if line is None:
         return
-    if not args.no_cpu_baseline and ws == 1 and w["kind"] not in ("gatesweep", "hsweep", "learned"):
+    if not args.no_cpu_baseline and ws == 1 and w["kind"] not in ("gatesweep", "hsweep", "learned", "readout"):
         line["cpu_baseline"] = oracle_sample(w, budget_s=args.cpu_budget)
     print(json.dumps(line))
 

@@ -276,7 +276,9 @@ __global__ void __launch_bounds__(kRedThreads) probs_kernel(const typename Cx<R>
         const auto v = a[x];
         const double p = (double)v.x * (double)v.x + (double)v.y * (double)v.y;
         uint32_t m = 0;
-        for (int j = 0; j < nq; ++j) m |= uint32_t((x >> pos[j]) & 1) << j;
+#pragma unroll
+        for (int j = 0; j < 32; ++j)  // unrolled so that pos[] stays in registers
+            if (j < nq) m |= uint32_t((x >> pos[j]) & 1) << j;
         if (use_smem) atomicAdd(&sh[m], p);
         else atomicAdd(&hist[m], p);
     }
@@ -284,6 +286,65 @@ __global__ void __launch_bounds__(kRedThreads) probs_kernel(const typename Cx<R>
         __syncthreads();
         for (int m = threadIdx.x; m < M; m += blockDim.x)
             if (sh[m] != 0.0) atomicAdd(&hist[m], sh[m]);
+    }
+}
+
+// Marginals over at most Q qubits (2^Q bins): each thread keeps its bins in registers
+// (branch-free select-and-add per bin), then the bins are reduced with warp shuffles and added
+// to the global histogram with one FP64 atomic per warp and bin.
+template <typename R, int Q>
+__global__ void __launch_bounds__(kRedThreads) probs_small_kernel(const typename Cx<R>::T *__restrict__ a,
+                                                                  uint64_t N, int nq, uint4 pos_packed0,
+                                                                  double *__restrict__ hist)
+{
+    constexpr int M = 1 << Q;
+    uint32_t pos[Q];
+    const uint32_t w[4] = {pos_packed0.x, pos_packed0.y, pos_packed0.z, pos_packed0.w};
+#pragma unroll
+    for (int j = 0; j < Q; ++j) pos[j] = (w[j >> 2] >> (8 * (j & 3))) & 0xff;
+    // complex64: FP32 partial sums of at most 32 amplitudes per bin, then FP64 (the FP64 pipe
+    // is 1/64 of the FP32 rate on this part); complex128: FP64 throughout
+    double acc[M];
+    R part[M];
+#pragma unroll
+    for (int b = 0; b < M; ++b) {
+        acc[b] = 0.0;
+        part[b] = R(0);
+    }
+    int cnt = 0;
+    const uint64_t per = (N + gridDim.x - 1) / gridDim.x;
+    const uint64_t lo = per * blockIdx.x;
+    const uint64_t hi = lo + per < N ? lo + per : N;
+    for (uint64_t x = lo + threadIdx.x; x < hi; x += blockDim.x) {
+        const auto v = a[x];
+        const R p = (R)v.x * (R)v.x + (R)v.y * (R)v.y;
+        uint32_t m = 0;
+#pragma unroll
+        for (int j = 0; j < Q; ++j)
+            if (j < nq) m |= uint32_t((x >> pos[j]) & 1) << j;
+        if (sizeof(R) == 8) {
+#pragma unroll
+            for (int b = 0; b < M; ++b) acc[b] += (m == uint32_t(b)) ? (double)p : 0.0;
+        } else {
+#pragma unroll
+            for (int b = 0; b < M; ++b) part[b] += (m == uint32_t(b)) ? p : R(0);
+            if (++cnt == 32) {
+#pragma unroll
+                for (int b = 0; b < M; ++b) {
+                    acc[b] += (double)part[b];
+                    part[b] = R(0);
+                }
+                cnt = 0;
+            }
+        }
+    }
+#pragma unroll
+    for (int b = 0; b < M; ++b) acc[b] += (double)part[b];
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int b = 0; b < M; ++b) {
+        const double t = warp_sum(acc[b]);
+        if (lane == 0 && b < (1 << nq) && t != 0.0) atomicAdd(&hist[b], t);
     }
 }
 
@@ -357,12 +418,23 @@ int launch_probs(const LaunchCtx &c, const int *phys_q, int nq, double *d_scratc
         return cuda_fail("probs memset", err, errlen);
     const int blocks = reduce_blocks(N);
     const size_t smem = nq <= 11 ? M * sizeof(double) : 0;
-    if (c.dt == QS_C64)
+    if (nq <= 3) {
+        if (c.dt == QS_C64)
+            probs_small_kernel<float, 3><<<blocks, kRedThreads, 0, st>>>((const float2 *)c.amp, N, nq, p0, d_scratch);
+        else
+            probs_small_kernel<double, 3><<<blocks, kRedThreads, 0, st>>>((const double2 *)c.amp, N, nq, p0, d_scratch);
+    } else if (nq <= 5) {
+        if (c.dt == QS_C64)
+            probs_small_kernel<float, 5><<<blocks, kRedThreads, 0, st>>>((const float2 *)c.amp, N, nq, p0, d_scratch);
+        else
+            probs_small_kernel<double, 5><<<blocks, kRedThreads, 0, st>>>((const double2 *)c.amp, N, nq, p0, d_scratch);
+    } else if (c.dt == QS_C64) {
         probs_kernel<float><<<blocks, kRedThreads, smem, st>>>((const float2 *)c.amp, N, nq, p0, p1,
                                                                d_scratch);
-    else
+    } else {
         probs_kernel<double><<<blocks, kRedThreads, smem, st>>>((const double2 *)c.amp, N, nq, p0,
                                                                 p1, d_scratch);
+    }
     int rc = cuda_fail("probs launch", err, errlen);
     if (rc) return rc;
     if (cudaMemcpyAsync(h_out, d_scratch, M * sizeof(double), cudaMemcpyDeviceToHost, st) !=
