@@ -176,31 +176,56 @@ struct ParityTables {
     uint32_t col[64][kParityMaxTerms / 32];  // parity columns of the physical bits
     double csum_re, csum_im;                 // sum of all coefficients
     int nbytes;                              // table bytes in use
-    int pad;
+    int incremental;                         // 1: every walked bit touches at most 4 table bytes
     double tre[kParityBytes][256], tim[kParityBytes][256];
+    double cb_re[64], cb_im[64];             // sum of the coefficients of the terms containing bit b
+    uint32_t bbytes[64];                     // table bytes those terms occupy (4 x 8 bits, 0xff = none)
 };
 
 // Each block owns 2^(8 + klog) consecutive amplitudes; thread t visits lo | (gray(i) << 8) | t for
-// i = 0 .. 2^klog - 1, so consecutive visits differ in one index bit and the parity vector
-// changes by one column (one XOR per word); the warp's 32 amplitudes stay contiguous.
-template <typename R>
+// i = 0 .. 2^klog - 1, so consecutive visits differ in one index bit b and the parity vector
+// changes by one column (one XOR per word); the warp's 32 amplitudes stay contiguous.  Only the
+// terms containing b change sign, so h(x) is updated rather than recomputed:
+//   h_new = h + 2 C_b - 4 S(p & col_b),
+// with C_b the sum of their coefficients and S(.) read from the byte tables over the (at most
+// four) bytes where col_b is nonzero.  Every 32 visits h is recomputed from all bytes, which
+// bounds the rounding drift of the updates.
+// Byte b of a parity vector held in NW registers (selects, no local memory).
+template <int NW>
+__device__ __forceinline__ uint32_t parity_byte(const uint32_t (&Q)[NW], int b)
+{
+    uint32_t word = Q[0];
+#pragma unroll
+    for (int w = 1; w < NW; ++w)
+        if ((b >> 2) == w) word = Q[w];
+    return (word >> (8 * (b & 3))) & 0xffu;
+}
+
+template <typename R, int NW, bool CIM>
 __global__ void __launch_bounds__(kRedThreads) expect_parity_kernel(const typename Cx<R>::T *__restrict__ a,
                                                                     uint64_t xm, int klog,
                                                                     const ParityTables *__restrict__ pt,
                                                                     double *__restrict__ part)
 {
-    constexpr int NW = kParityMaxTerms / 32;
     extern __shared__ __align__(16) unsigned char dyn[];
     R *tre = reinterpret_cast<R *>(dyn);
     const int nb = pt->nbytes;
     R *tim = tre + nb * 256;
     __shared__ uint32_t col[64][NW];
+    __shared__ R cbr[64], cbi[64];
+    __shared__ uint32_t bby[64];
     for (int j = threadIdx.x; j < nb * 256; j += blockDim.x) {
         tre[j] = (R)pt->tre[j >> 8][j & 255];
-        tim[j] = (R)pt->tim[j >> 8][j & 255];
+        if (CIM) tim[j] = (R)pt->tim[j >> 8][j & 255];
     }
     for (int j = threadIdx.x; j < 64 * NW; j += blockDim.x) col[j / NW][j % NW] = pt->col[j / NW][j % NW];
+    for (int j = threadIdx.x; j < 64; j += blockDim.x) {
+        cbr[j] = (R)pt->cb_re[j];
+        cbi[j] = (R)pt->cb_im[j];
+        bby[j] = pt->bbytes[j];
+    }
     __syncthreads();
+    const bool inc = pt->incremental != 0;
     const R cre0 = (R)pt->csum_re, cim0 = (R)pt->csum_im;
     const uint64_t lo = uint64_t(blockIdx.x) << (8 + klog);
     const uint64_t x0 = lo | threadIdx.x;
@@ -212,27 +237,48 @@ __global__ void __launch_bounds__(kRedThreads) expect_parity_kernel(const typena
 #pragma unroll
             for (int w = 0; w < NW; ++w) P[w] ^= col[i][w];
     double accr = 0.0, acci = 0.0;
-    R fr = 0, fi = 0;
+    R fr = 0, fi = 0, er = 0, ei = 0;
     int cnt = 0;
     const uint32_t K = 1u << klog;
     for (uint32_t i = 0; i < K; ++i) {
+        int bit = -1;
         if (i) {
-            const int bit = 8 + __ffs(i) - 1;
+            bit = 8 + __ffs(i) - 1;
 #pragma unroll
             for (int w = 0; w < NW; ++w) P[w] ^= col[bit][w];
+        }
+        if (!inc || (i & 31u) == 0) {
+            R sr = 0, si = 0;
+            for (int b = 0; b < nb; ++b) {
+                const uint32_t v = parity_byte<NW>(P, b);
+                sr += tre[b * 256 + v];
+                if (CIM) si += tim[b * 256 + v];
+            }
+            er = cre0 - R(2) * sr;
+            ei = CIM ? cim0 - R(2) * si : R(0);
+        } else {
+            uint32_t M[NW];
+#pragma unroll
+            for (int w = 0; w < NW; ++w) M[w] = P[w] & col[bit][w];
+            const uint32_t bl = bby[bit];
+            R sr = 0, si = 0;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const uint32_t b = (bl >> (8 * k)) & 0xffu;
+                if (b != 0xffu) {
+                    const uint32_t v = parity_byte<NW>(M, int(b));
+                    sr += tre[b * 256 + v];
+                    if (CIM) si += tim[b * 256 + v];
+                }
+            }
+            er += R(2) * cbr[bit] - R(4) * sr;
+            if (CIM) ei += R(2) * cbi[bit] - R(4) * si;
         }
         const uint64_t x = x0 | (uint64_t(i ^ (i >> 1)) << 8);
         const auto ax = a[x];
         const auto ay = a[x ^ xm];
         const R vr = (R)ay.x * (R)ax.x + (R)ay.y * (R)ax.y;
         const R vi = (R)ay.x * (R)ax.y - (R)ay.y * (R)ax.x;
-        R sr = 0, si = 0;
-        for (int b = 0; b < nb; ++b) {
-            const uint32_t v = (P[b >> 2] >> (8 * (b & 3))) & 0xffu;
-            sr += tre[b * 256 + v];
-            si += tim[b * 256 + v];
-        }
-        const R er = cre0 - R(2) * sr, ei = cim0 - R(2) * si;
         fr += er * vr - ei * vi;
         fi += er * vi + ei * vr;
         if (sizeof(R) == 4 && ++cnt == 32) {
@@ -444,6 +490,42 @@ int launch_probs(const LaunchCtx &c, const int *phys_q, int nq, double *d_scratc
     return QS_OK;
 }
 
+namespace {
+
+template <typename R, int NW, bool CIM>
+void launch_parity_t(const typename Cx<R>::T *a, uint64_t xm, int klog, const ParityTables *pt, double *part,
+                     int nblk, size_t dsm, cudaStream_t st)
+{
+    static int attr_dev = -1;  // tables of up to 16 bytes x 256 x 2 doubles = 64 KiB
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (attr_dev != dev) {
+        cudaFuncSetAttribute(expect_parity_kernel<R, NW, CIM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             kParityBytes * 256 * 2 * int(sizeof(double)));
+        attr_dev = dev;
+    }
+    expect_parity_kernel<R, NW, CIM><<<nblk, kRedThreads, dsm, st>>>(a, xm, klog, pt, part);
+}
+
+template <typename R>
+int launch_parity(const typename Cx<R>::T *a, uint64_t xm, int klog, const ParityTables *pt, double *part, int nblk,
+                  size_t dsm, int nw, bool cim, cudaStream_t st)
+{
+    if (nw == 1) {
+        if (cim) launch_parity_t<R, 1, true>(a, xm, klog, pt, part, nblk, dsm, st);
+        else launch_parity_t<R, 1, false>(a, xm, klog, pt, part, nblk, dsm, st);
+    } else if (nw == 2) {
+        if (cim) launch_parity_t<R, 2, true>(a, xm, klog, pt, part, nblk, dsm, st);
+        else launch_parity_t<R, 2, false>(a, xm, klog, pt, part, nblk, dsm, st);
+    } else {
+        if (cim) launch_parity_t<R, 4, true>(a, xm, klog, pt, part, nblk, dsm, st);
+        else launch_parity_t<R, 4, false>(a, xm, klog, pt, part, nblk, dsm, st);
+    }
+    return QS_OK;
+}
+
+}  // namespace
+
 int launch_expect(const LaunchCtx &c, const uint64_t *xm, const uint64_t *zm, const double *coeff,
                   size_t nterms, double *d_scratch, size_t scratch_bytes, double *h_out, char *err,
                   size_t errlen)
@@ -477,6 +559,7 @@ int launch_expect(const LaunchCtx &c, const uint64_t *xm, const uint64_t *zm, co
             hg.nterms++;
         }
         int nblk = blocks;
+        int rc_launch = QS_OK;
         if (hg.nterms >= 8 && hg.nterms <= kParityMaxTerms && c.n >= 16) {
             // parity tables (host, FP64), then the Gray-walk kernel
             ParityTables &pt = hpt[0];
@@ -497,26 +580,37 @@ int launch_expect(const LaunchCtx &c, const uint64_t *xm, const uint64_t *zm, co
                             pt.tim[b][v] += hg.cim[t];
                         }
                     }
+            // per bit: the coefficient sum of the terms containing it and the table bytes they use
+            bool cim = false;
+            for (int t = 0; t < hg.nterms; ++t) cim = cim || hg.cim[t] != 0.0;
+            pt.incremental = 1;
+            for (int i = 0; i < 64; ++i) {
+                uint32_t list = 0xffffffffu;
+                int nbk = 0;
+                for (int t = 0; t < hg.nterms; ++t)
+                    if (hg.zm[t] >> i & 1) {
+                        pt.cb_re[i] += hg.cre[t];
+                        pt.cb_im[i] += hg.cim[t];
+                    }
+                for (int b = 0; b < pt.nbytes; ++b)
+                    if ((pt.col[i][b >> 2] >> (8 * (b & 3))) & 0xffu) {
+                        if (nbk < 4) list = (list & ~(0xffu << (8 * nbk))) | (uint32_t(b) << (8 * nbk));
+                        ++nbk;
+                    }
+                if (nbk > 4) pt.incremental = 0;
+                pt.bbytes[i] = list;
+            }
             if (cudaMemcpyAsync(dpt, &pt, sizeof pt, cudaMemcpyHostToDevice, st) != cudaSuccess)
                 return cuda_fail("expect upload", err, errlen);
             const int blog = std::min(12, c.n - 12);
             nblk = 1 << blog;
             const int klog = c.n - blog - 8;
             const size_t dsm = size_t(pt.nbytes) * 256 * 2 * (c.dt == QS_C64 ? sizeof(float) : sizeof(double));
-            static int attr_dev = -1;  // tables of up to 16 bytes x 256 x 2 doubles = 64 KiB
-            int dev = 0;
-            cudaGetDevice(&dev);
-            if (attr_dev != dev) {
-                const int cap = kParityBytes * 256 * 2 * int(sizeof(double));
-                cudaFuncSetAttribute(expect_parity_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
-                cudaFuncSetAttribute(expect_parity_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
-                attr_dev = dev;
-            }
+            const int nw = hg.nterms <= 32 ? 1 : hg.nterms <= 64 ? 2 : 4;
             if (c.dt == QS_C64)
-                expect_parity_kernel<float><<<nblk, kRedThreads, dsm, st>>>((const float2 *)c.amp, hg.xm, klog, dpt, part);
+                rc_launch = launch_parity<float>((const float2 *)c.amp, hg.xm, klog, dpt, part, nblk, dsm, nw, cim, st);
             else
-                expect_parity_kernel<double><<<nblk, kRedThreads, dsm, st>>>((const double2 *)c.amp, hg.xm, klog, dpt,
-                                                                             part);
+                rc_launch = launch_parity<double>((const double2 *)c.amp, hg.xm, klog, dpt, part, nblk, dsm, nw, cim, st);
         } else {
             if (cudaMemcpyAsync(dgrp, &hg, sizeof(TermGroup), cudaMemcpyHostToDevice, st) != cudaSuccess)
                 return cuda_fail("expect upload", err, errlen);
