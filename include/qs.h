@@ -264,7 +264,10 @@ qs_status qs_probs_noalloc(const void *dev_amp, int n, qs_dtype dt, const int *q
 qs_status qs_sample(qs_state *s, const double *u, size_t shots, uint64_t *host_out);
 
 /* host_out[0] = Re sum_t coeff_t <psi|P_t|psi>, host_out[1] = its imaginary part (zero up to
- * rounding for Hermitian sums).  FP64 accumulation.  Synchronises. */
+ * rounding for Hermitian sums).  Terms are grouped by X mask (at most 256 per group) and each
+ * group costs one read of the state; groups of four or more terms on 16 or more qubits go
+ * through Walsh-Hadamard tiles, so that read costs the same whatever the group's size.  FP64
+ * accumulation across tiles (complex64 states: FP32 within a tile).  Synchronises. */
 qs_status qs_expect_pauli_sum(qs_state *s, const qs_pauli_term *terms, size_t nterms,
                               double *host_out);
 

@@ -4,6 +4,9 @@
 //  * probs:  marginal probabilities over a set of physical bit positions
 //  * expect: sum_t c_t <psi|P_t|psi> for Pauli strings, grouped by X mask so that one pass
 //            serves every term with the same X mask: P|x> = i^{#Y} (-1)^{popcount(x&z)} |x^xm>.
+//            Groups of four or more terms go through 1024-amplitude Walsh-Hadamard tiles, so
+//            the pass costs the same whatever the number of terms; smaller groups loop over
+//            their terms per amplitude.
 //
 // Accumulation: per-thread partial sums (FP64 for complex128; for complex64 at most 32 FP32
 // terms are summed before conversion to FP64), warp-shuffle and shared-memory tree per block,
@@ -57,31 +60,32 @@ __device__ __forceinline__ void block_sum2(double &a, double &b)
 }
 
 // Each block handles a contiguous range of amplitudes; thread t of the block reads elements
-// t, t + T, ... of that range (coalesced).
+// t, t + T, ... of that range (coalesced), kUnroll independent loads at a time.
+constexpr int kUnroll = 8;
 template <typename R>
 __global__ void __launch_bounds__(kRedThreads) norm2_kernel(const typename Cx<R>::T *__restrict__ a,
                                                             uint64_t N, double *__restrict__ part)
 {
+    using T = typename Cx<R>::T;
     const uint64_t per = (N + gridDim.x - 1) / gridDim.x;
     const uint64_t lo = per * blockIdx.x;
     const uint64_t hi = lo + per < N ? lo + per : N;
     double acc = 0.0;
-    if (sizeof(R) == 4) {
-        float f = 0.f;
-        int cnt = 0;
-        for (uint64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-            const auto v = a[i];
-            f = fmaf((float)v.x, (float)v.x, f);
-            f = fmaf((float)v.y, (float)v.y, f);
-            if (++cnt == 32) { acc += (double)f; f = 0.f; cnt = 0; }
+    for (uint64_t x0 = lo + threadIdx.x; x0 < hi; x0 += uint64_t(kUnroll) * blockDim.x) {
+        T v[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            const uint64_t x = x0 + uint64_t(u) * blockDim.x;
+            v[u] = x < hi ? a[x] : T{};
+        }
+        // complex64: the kUnroll squares are summed in FP32, then added in FP64
+        R f = 0;
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            f = fma(v[u].x, v[u].x, f);
+            f = fma(v[u].y, v[u].y, f);
         }
         acc += (double)f;
-    } else {
-        for (uint64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-            const auto v = a[i];
-            acc = fma((double)v.x, (double)v.x, acc);
-            acc = fma((double)v.y, (double)v.y, acc);
-        }
     }
     double dummy = 0.0;
     block_sum2(acc, dummy);
@@ -165,123 +169,159 @@ __global__ void __launch_bounds__(kRedThreads) expect_kernel(const typename Cx<R
     }
 }
 
-// Term parities as a linear map.  For a group of Z strings with the same X mask, the sign of term
-// t at index x is (-1)^{p_t(x)} with p_t(x) = popcount(x & zm_t) mod 2, linear over GF(2) in x:
-// the parity vector p(x) (one bit per term) is the XOR of the columns col[i] of the bits i set
-// in x.  With h(x) = sum_t c_t (-1)^{p_t} = sum_t c_t - 2 sum_{t : p_t = 1} c_t, the second sum
-// is read from byte tables: tab[b][v] = sum of c_{8b+k} over the set bits k of v.
-constexpr int kParityMaxTerms = 128;
-constexpr int kParityBytes = kParityMaxTerms / 8;
-struct ParityTables {
-    uint32_t col[64][kParityMaxTerms / 32];  // parity columns of the physical bits
-    double csum_re, csum_im;                 // sum of all coefficients
-    int nbytes;                              // table bytes in use
-    int incremental;                         // 1: every walked bit touches at most 4 table bytes
-    double tre[kParityBytes][256], tim[kParityBytes][256];
-    double cb_re[64], cb_im[64];             // sum of the coefficients of the terms containing bit b
-    uint32_t bbytes[64];                     // table bytes those terms occupy (4 x 8 bits, 0xff = none)
+// Walsh-Hadamard form of one X-mask group.  Write an index as x = (H, L) with L its low 10 bits
+// and split each Z mask the same way, z_t = (zh_t, zl_t).  With v(x) = conj(a[x^xm]) a[x],
+//   sum_x v(x) sum_t C_t (-1)^{popc(x & z_t)} = sum_H sum_t C_t s_t(H) Vhat_H(zl_t),
+// where s_t(H) = (-1)^{popc(H & zh_t)} and Vhat_H is the Walsh-Hadamard transform of v(H, .)
+// over the 1024 values of L.  One warp transforms one tile (10 butterfly stages: the bits held
+// in a lane's 32 registers, then the five lane bits through shuffles), writes Vhat to shared
+// memory and then spends one lookup per term, so the per-amplitude work no longer grows with
+// the number of terms.
+//   When xm has a bit p >= 10, the tiles with bit p of the index clear are paired with their
+// partners H ^ (xm >> 10): the partner's v is conj(v) and its term signs are those of x times
+// (-1)^{popc(xm & z_t)}, so one tile pass covers both and every amplitude is read once.  The
+// host folds both into four real coefficients per term: re += A Vr + B Vi, im += C Vi + D Vr.
+constexpr int kWhtTileLog = 10;
+struct WhtTerms {
+    uint64_t xm;
+    int nterms;
+    int pair;
+    uint64_t zh[kMaxTermsPerGroup];
+    uint32_t zl[kMaxTermsPerGroup];
+    double q[4][kMaxTermsPerGroup];
 };
 
-// Each block owns 2^(8 + klog) consecutive amplitudes; thread t visits lo | (gray(i) << 8) | t for
-// i = 0 .. 2^klog - 1, so consecutive visits differ in one index bit b and the parity vector
-// changes by one column (one XOR per word); the warp's 32 amplitudes stay contiguous.  Only the
-// terms containing b change sign, so h(x) is updated rather than recomputed:
-//   h_new = h + 2 C_b - 4 S(p & col_b),
-// with C_b the sum of their coefficients and S(.) read from the byte tables over the (at most
-// four) bytes where col_b is nonzero.  Every 32 visits h is recomputed from all bytes, which
-// bounds the rounding drift of the updates.
-// Byte b of a parity vector held in NW registers (selects, no local memory).
-template <int NW>
-__device__ __forceinline__ uint32_t parity_byte(const uint32_t (&Q)[NW], int b)
+// Asks the L2 to fetch [p, p + bytes) (p 16-byte aligned, bytes a multiple of 16); nothing is
+// written to the SM and nothing waits for it.
+__device__ __forceinline__ void prefetch_l2_bulk(const void *p, uint32_t bytes)
 {
-    uint32_t word = Q[0];
-#pragma unroll
-    for (int w = 1; w < NW; ++w)
-        if ((b >> 2) == w) word = Q[w];
-    return (word >> (8 * (b & 3))) & 0xffu;
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(__cvta_generic_to_global(p)), "r"(bytes)
+                 : "memory");
 }
 
-template <typename R, int NW, bool CIM>
-__global__ void __launch_bounds__(kRedThreads) expect_parity_kernel(const typename Cx<R>::T *__restrict__ a,
-                                                                    uint64_t xm, int klog,
-                                                                    const ParityTables *__restrict__ pt,
-                                                                    double *__restrict__ part)
+template <typename R, bool CPLX>
+__global__ void __launch_bounds__(kRedThreads) expect_wht_kernel(const typename Cx<R>::T *__restrict__ a, int n,
+                                                                 const WhtTerms *__restrict__ wt,
+                                                                 double *__restrict__ part)
 {
+    using T = typename Cx<R>::T;
+    constexpr int VL = sizeof(T) == 8 ? 1 : 0;  // complex64: two amplitudes per 16-byte load
+    constexpr int NV = 32 >> VL;                // vector loads per lane per tile
     extern __shared__ __align__(16) unsigned char dyn[];
-    R *tre = reinterpret_cast<R *>(dyn);
-    const int nb = pt->nbytes;
-    R *tim = tre + nb * 256;
-    __shared__ uint32_t col[64][NW];
-    __shared__ R cbr[64], cbi[64];
-    __shared__ uint32_t bby[64];
-    for (int j = threadIdx.x; j < nb * 256; j += blockDim.x) {
-        tre[j] = (R)pt->tre[j >> 8][j & 255];
-        if (CIM) tim[j] = (R)pt->tim[j >> 8][j & 255];
-    }
-    for (int j = threadIdx.x; j < 64 * NW; j += blockDim.x) col[j / NW][j % NW] = pt->col[j / NW][j % NW];
-    for (int j = threadIdx.x; j < 64; j += blockDim.x) {
-        cbr[j] = (R)pt->cb_re[j];
-        cbi[j] = (R)pt->cb_im[j];
-        bby[j] = pt->bbytes[j];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    R *wr = reinterpret_cast<R *>(dyn) + (warp << kWhtTileLog) * (CPLX ? 2 : 1);
+    R *wi = wr + (1 << kWhtTileLog);
+    __shared__ uint64_t zh[kMaxTermsPerGroup];
+    __shared__ uint32_t zl[kMaxTermsPerGroup];
+    __shared__ R q[4][kMaxTermsPerGroup];
+    const int nt = wt->nterms;
+    for (int j = threadIdx.x; j < nt; j += blockDim.x) {
+        zh[j] = wt->zh[j];
+        zl[j] = wt->zl[j];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) q[k][j] = (R)wt->q[k][j];
     }
     __syncthreads();
-    const bool inc = pt->incremental != 0;
-    const R cre0 = (R)pt->csum_re, cim0 = (R)pt->csum_im;
-    const uint64_t lo = uint64_t(blockIdx.x) << (8 + klog);
-    const uint64_t x0 = lo | threadIdx.x;
-    uint32_t P[NW];
-#pragma unroll
-    for (int w = 0; w < NW; ++w) P[w] = 0;
-    for (int i = 0; i < 64; ++i)
-        if (x0 >> i & 1)
-#pragma unroll
-            for (int w = 0; w < NW; ++w) P[w] ^= col[i][w];
+    const uint64_t xm = wt->xm, xmh = xm >> kWhtTileLog;
+    const uint32_t xml = uint32_t(xm) & ((1u << kWhtTileLog) - 1);
+    const bool pair = wt->pair != 0;
+    const int p = pair ? 63 - __clzll((long long)xmh) : 0;
+    const uint64_t ntiles = 1ull << (n - kWhtTileLog - (pair ? 1 : 0));
+    const uint64_t nwarps = uint64_t(gridDim.x) * (blockDim.x >> 5);
     double accr = 0.0, acci = 0.0;
-    R fr = 0, fi = 0, er = 0, ei = 0;
+    R fr = 0, fi = 0;
     int cnt = 0;
-    const uint32_t K = 1u << klog;
-    for (uint32_t i = 0; i < K; ++i) {
-        int bit = -1;
-        if (i) {
-            bit = 8 + __ffs(i) - 1;
+    for (uint64_t tile = uint64_t(blockIdx.x) * (blockDim.x >> 5) + warp; tile < ntiles; tile += nwarps) {
+        const uint64_t H = pair ? ((tile >> p) << (p + 1)) | (tile & ((1ull << p) - 1)) : tile;
+        const T *at = a + (H << kWhtTileLog);
+        const T *ap = a + ((H ^ xmh) << kWhtTileLog);
+        // the warp's next tile moves into L2 while this one is transformed (paired tiles already
+        // keep two tiles of loads in flight and ran slower with it: 1.34 -> 1.69 ms at 30 qubits)
+        if (!pair && lane == 0 && tile + nwarps < ntiles)
+            prefetch_l2_bulk(a + ((tile + nwarps) << kWhtTileLog), uint32_t(sizeof(T)) << kWhtTileLog);
+        // element j of the lane sits at L = (j & VL) | lane << VL | (j >> VL) << (5 + VL)
+        R vr[32], vi[32];
 #pragma unroll
-            for (int w = 0; w < NW; ++w) P[w] ^= col[bit][w];
-        }
-        if (!inc || (i & 31u) == 0) {
-            R sr = 0, si = 0;
-            for (int b = 0; b < nb; ++b) {
-                const uint32_t v = parity_byte<NW>(P, b);
-                sr += tre[b * 256 + v];
-                if (CIM) si += tim[b * 256 + v];
-            }
-            er = cre0 - R(2) * sr;
-            ei = CIM ? cim0 - R(2) * si : R(0);
-        } else {
-            uint32_t M[NW];
-#pragma unroll
-            for (int w = 0; w < NW; ++w) M[w] = P[w] & col[bit][w];
-            const uint32_t bl = bby[bit];
-            R sr = 0, si = 0;
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const uint32_t b = (bl >> (8 * k)) & 0xffu;
-                if (b != 0xffu) {
-                    const uint32_t v = parity_byte<NW>(M, int(b));
-                    sr += tre[b * 256 + v];
-                    if (CIM) si += tim[b * 256 + v];
+        for (int k = 0; k < NV; ++k) {
+            const uint32_t L0 = (uint32_t(lane) << VL) | (uint32_t(k) << (5 + VL));
+            if constexpr (VL != 0) {
+                const float4 x = *reinterpret_cast<const float4 *>(at + L0);
+                if constexpr (CPLX) {
+                    const uint32_t Lp = (L0 ^ xml) & ~1u;
+                    float4 y = *reinterpret_cast<const float4 *>(ap + Lp);
+                    if (xml & 1u) y = make_float4(y.z, y.w, y.x, y.y);
+                    vr[2 * k] = (R)(y.x * x.x + y.y * x.y);
+                    vi[2 * k] = (R)(y.x * x.y - y.y * x.x);
+                    vr[2 * k + 1] = (R)(y.z * x.z + y.w * x.w);
+                    vi[2 * k + 1] = (R)(y.z * x.w - y.w * x.z);
+                } else {
+                    vr[2 * k] = (R)(x.x * x.x + x.y * x.y);
+                    vr[2 * k + 1] = (R)(x.z * x.z + x.w * x.w);
+                }
+            } else {
+                const T x = at[L0];
+                if (CPLX) {
+                    const T y = ap[L0 ^ xml];
+                    vr[k] = (R)(y.x * x.x + y.y * x.y);
+                    vi[k] = (R)(y.x * x.y - y.y * x.x);
+                } else {
+                    vr[k] = (R)(x.x * x.x + x.y * x.y);
                 }
             }
-            er += R(2) * cbr[bit] - R(4) * sr;
-            if (CIM) ei += R(2) * cbi[bit] - R(4) * si;
         }
-        const uint64_t x = x0 | (uint64_t(i ^ (i >> 1)) << 8);
-        const auto ax = a[x];
-        const auto ay = a[x ^ xm];
-        const R vr = (R)ay.x * (R)ax.x + (R)ay.y * (R)ax.y;
-        const R vi = (R)ay.x * (R)ax.y - (R)ay.y * (R)ax.x;
-        fr += er * vr - ei * vi;
-        fi += er * vi + ei * vr;
-        if (sizeof(R) == 4 && ++cnt == 32) {
+        // butterflies over the five register bits ...
+#pragma unroll
+        for (int s = 0; s < 5; ++s)
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+                if (!(j >> s & 1)) {
+                    const int k = j | (1 << s);
+                    const R r0 = vr[j], r1 = vr[k];
+                    vr[j] = r0 + r1;
+                    vr[k] = r0 - r1;
+                    if (CPLX) {
+                        const R i0 = vi[j], i1 = vi[k];
+                        vi[j] = i0 + i1;
+                        vi[k] = i0 - i1;
+                    }
+                }
+        // ... and over the five lane bits (the lane with the bit set keeps the difference)
+#pragma unroll
+        for (int s = 0; s < 5; ++s) {
+            const R sg = (lane >> s & 1) ? R(-1) : R(1);
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                vr[j] = fma(sg, vr[j], __shfl_xor_sync(0xffffffffu, vr[j], 1 << s));
+                if (CPLX) vi[j] = fma(sg, vi[j], __shfl_xor_sync(0xffffffffu, vi[j], 1 << s));
+            }
+        }
+        // Vhat(m) sits where v(L = m) was
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            const uint32_t L0 = (uint32_t(lane) << VL) | (uint32_t(k) << (5 + VL));
+            if constexpr (VL != 0) {
+                *reinterpret_cast<float2 *>(wr + L0) = make_float2((float)vr[2 * k], (float)vr[2 * k + 1]);
+                if (CPLX) *reinterpret_cast<float2 *>(wi + L0) = make_float2((float)vi[2 * k], (float)vi[2 * k + 1]);
+            } else {
+                wr[L0] = vr[k];
+                if (CPLX) wi[L0] = vi[k];
+            }
+        }
+        __syncwarp();
+        for (int t = lane; t < nt; t += 32) {
+            const uint32_t m = zl[t];
+            const R s = (__popcll(H & zh[t]) & 1) ? R(-1) : R(1);
+            const R Vr = wr[m];
+            if (CPLX) {
+                const R Vi = wi[m];
+                fr = fma(s, fma(q[0][t], Vr, q[1][t] * Vi), fr);
+                fi = fma(s, fma(q[2][t], Vi, q[3][t] * Vr), fi);
+            } else {
+                fr = fma(s * q[0][t], Vr, fr);
+            }
+        }
+        __syncwarp();
+        if (sizeof(R) == 4 && ++cnt == 8) {
             accr += (double)fr;
             acci += (double)fi;
             fr = fi = 0;
@@ -361,27 +401,38 @@ __global__ void __launch_bounds__(kRedThreads) probs_small_kernel(const typename
     const uint64_t per = (N + gridDim.x - 1) / gridDim.x;
     const uint64_t lo = per * blockIdx.x;
     const uint64_t hi = lo + per < N ? lo + per : N;
-    for (uint64_t x = lo + threadIdx.x; x < hi; x += blockDim.x) {
-        const auto v = a[x];
-        const R p = (R)v.x * (R)v.x + (R)v.y * (R)v.y;
-        uint32_t m = 0;
+    constexpr int U = 4;  // independent loads in flight per thread
+    using T = typename Cx<R>::T;
+    for (uint64_t x0 = lo + threadIdx.x; x0 < hi; x0 += uint64_t(U) * blockDim.x) {
+        T v[U];
 #pragma unroll
-        for (int j = 0; j < Q; ++j)
-            if (j < nq) m |= uint32_t((x >> pos[j]) & 1) << j;
-        if (sizeof(R) == 8) {
+        for (int u = 0; u < U; ++u) {
+            const uint64_t x = x0 + uint64_t(u) * blockDim.x;
+            v[u] = x < hi ? a[x] : T{};  // past the range: weight 0
+        }
 #pragma unroll
-            for (int b = 0; b < M; ++b) acc[b] += (m == uint32_t(b)) ? (double)p : 0.0;
-        } else {
+        for (int u = 0; u < U; ++u) {
+            const uint64_t x = x0 + uint64_t(u) * blockDim.x;
+            const R p = (R)v[u].x * (R)v[u].x + (R)v[u].y * (R)v[u].y;
+            uint32_t m = 0;
 #pragma unroll
-            for (int b = 0; b < M; ++b) part[b] += (m == uint32_t(b)) ? p : R(0);
-            if (++cnt == 32) {
+            for (int j = 0; j < Q; ++j)
+                if (j < nq) m |= uint32_t((x >> pos[j]) & 1) << j;
+            if (sizeof(R) == 8) {
 #pragma unroll
-                for (int b = 0; b < M; ++b) {
-                    acc[b] += (double)part[b];
-                    part[b] = R(0);
-                }
-                cnt = 0;
+                for (int b = 0; b < M; ++b) acc[b] += (m == uint32_t(b)) ? (double)p : 0.0;
+            } else {
+#pragma unroll
+                for (int b = 0; b < M; ++b) part[b] += (m == uint32_t(b)) ? p : R(0);
             }
+        }
+        if (sizeof(R) == 4 && (cnt += U) >= 32) {
+#pragma unroll
+            for (int b = 0; b < M; ++b) {
+                acc[b] += (double)part[b];
+                part[b] = R(0);
+            }
+            cnt = 0;
         }
     }
 #pragma unroll
@@ -422,8 +473,8 @@ int cuda_fail(const char *what, char *err, size_t errlen)
 
 size_t reduce_scratch_bytes()
 {
-    // partials (2 x blocks) + 2 results + one term group + its parity tables
-    return sizeof(double) * (2 * kRedBlocksMax + 8) + sizeof(TermGroup) + 256 + sizeof(ParityTables) + 256;
+    // partials (2 x blocks) + 2 results + one term group + its Walsh-Hadamard term table
+    return sizeof(double) * (2 * kRedBlocksMax + 8) + sizeof(TermGroup) + 256 + sizeof(WhtTerms) + 256;
 }
 
 int launch_norm2(const LaunchCtx &c, double *d_scratch, double *h_out, char *err, size_t errlen)
@@ -492,36 +543,36 @@ int launch_probs(const LaunchCtx &c, const int *phys_q, int nq, double *d_scratc
 
 namespace {
 
-template <typename R, int NW, bool CIM>
-void launch_parity_t(const typename Cx<R>::T *a, uint64_t xm, int klog, const ParityTables *pt, double *part,
-                     int nblk, size_t dsm, cudaStream_t st)
+template <typename R, bool CPLX>
+int launch_wht_t(const typename Cx<R>::T *a, int n, const WhtTerms *wt, uint64_t ntiles, double *part,
+                 cudaStream_t st)
 {
-    static int attr_dev = -1;  // tables of up to 16 bytes x 256 x 2 doubles = 64 KiB
+    const size_t dsm = (size_t(kRedThreads / 32) << kWhtTileLog) * sizeof(R) * (CPLX ? 2 : 1);
+    static int attr_dev = -1, per_sm = 1;
     int dev = 0;
     cudaGetDevice(&dev);
     if (attr_dev != dev) {
-        cudaFuncSetAttribute(expect_parity_kernel<R, NW, CIM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             kParityBytes * 256 * 2 * int(sizeof(double)));
+        cudaFuncSetAttribute(expect_wht_kernel<R, CPLX>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(dsm));
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, expect_wht_kernel<R, CPLX>, kRedThreads, dsm) !=
+                cudaSuccess ||
+            per_sm < 1)
+            per_sm = 1;
         attr_dev = dev;
     }
-    expect_parity_kernel<R, NW, CIM><<<nblk, kRedThreads, dsm, st>>>(a, xm, klog, pt, part);
+    reduce_blocks(1);  // reads the SM count once
+    uint64_t nb = uint64_t(g_sms) * uint64_t(per_sm);
+    const uint64_t need = std::max<uint64_t>(1, ntiles / (kRedThreads / 32));
+    nb = std::min<uint64_t>(std::min<uint64_t>(nb, need), kRedBlocksMax);
+    expect_wht_kernel<R, CPLX><<<int(nb), kRedThreads, dsm, st>>>(a, n, wt, part);
+    return int(nb);
 }
 
 template <typename R>
-int launch_parity(const typename Cx<R>::T *a, uint64_t xm, int klog, const ParityTables *pt, double *part, int nblk,
-                  size_t dsm, int nw, bool cim, cudaStream_t st)
+int launch_wht(const typename Cx<R>::T *a, int n, const WhtTerms *wt, bool cplx, uint64_t ntiles, double *part,
+               cudaStream_t st)
 {
-    if (nw == 1) {
-        if (cim) launch_parity_t<R, 1, true>(a, xm, klog, pt, part, nblk, dsm, st);
-        else launch_parity_t<R, 1, false>(a, xm, klog, pt, part, nblk, dsm, st);
-    } else if (nw == 2) {
-        if (cim) launch_parity_t<R, 2, true>(a, xm, klog, pt, part, nblk, dsm, st);
-        else launch_parity_t<R, 2, false>(a, xm, klog, pt, part, nblk, dsm, st);
-    } else {
-        if (cim) launch_parity_t<R, 4, true>(a, xm, klog, pt, part, nblk, dsm, st);
-        else launch_parity_t<R, 4, false>(a, xm, klog, pt, part, nblk, dsm, st);
-    }
-    return QS_OK;
+    return cplx ? launch_wht_t<R, true>(a, n, wt, ntiles, part, st)
+                : launch_wht_t<R, false>(a, n, wt, ntiles, part, st);
 }
 
 }  // namespace
@@ -538,8 +589,8 @@ int launch_expect(const LaunchCtx &c, const uint64_t *xm, const uint64_t *zm, co
     const int blocks = reduce_blocks(N);
     std::vector<TermGroup> hgv(1);  // host staging; each copy completes before reuse
     TermGroup &hg = hgv[0];
-    std::vector<ParityTables> hpt(1);
-    ParityTables *dpt = reinterpret_cast<ParityTables *>(
+    std::vector<WhtTerms> hw(1);
+    WhtTerms *dpt = reinterpret_cast<WhtTerms *>(
         (reinterpret_cast<uintptr_t>(dgrp) + sizeof(TermGroup) + 255) & ~uintptr_t(255));
     double tot_r = 0.0, tot_i = 0.0;
     std::vector<char> done(nterms, 0);
@@ -559,58 +610,33 @@ int launch_expect(const LaunchCtx &c, const uint64_t *xm, const uint64_t *zm, co
             hg.nterms++;
         }
         int nblk = blocks;
-        int rc_launch = QS_OK;
-        if (hg.nterms >= 8 && hg.nterms <= kParityMaxTerms && c.n >= 16) {
-            // parity tables (host, FP64), then the Gray-walk kernel
-            ParityTables &pt = hpt[0];
-            std::memset(&pt, 0, sizeof pt);
-            pt.nbytes = (hg.nterms + 7) / 8;
+        if (hg.nterms >= 4 && c.n >= 16) {
+            // Walsh-Hadamard tiles; coefficients folded on the host in FP64
+            WhtTerms &w = hw[0];
+            w.xm = hg.xm;
+            w.nterms = hg.nterms;
+            w.pair = (hg.xm >> kWhtTileLog) != 0;
             for (int t = 0; t < hg.nterms; ++t) {
-                pt.csum_re += hg.cre[t];
-                pt.csum_im += hg.cim[t];
-                for (int i = 0; i < 64; ++i)
-                    if (hg.zm[t] >> i & 1) pt.col[i][t >> 5] |= 1u << (t & 31);
+                w.zh[t] = hg.zm[t] >> kWhtTileLog;
+                w.zl[t] = uint32_t(hg.zm[t]) & ((1u << kWhtTileLog) - 1);
+                const double cr = hg.cre[t], ci = hg.cim[t];
+                // partner tile: coefficient times (-1)^{popc(xm & z)}; none without pairing
+                const double sg = (__builtin_popcountll(hg.xm & hg.zm[t]) & 1) ? -1.0 : 1.0;
+                const double pr = w.pair ? sg * cr : 0.0, pi = w.pair ? sg * ci : 0.0;
+                w.q[0][t] = cr + pr;
+                w.q[1][t] = pi - ci;
+                w.q[2][t] = cr - pr;
+                w.q[3][t] = ci + pi;
             }
-            for (int b = 0; b < pt.nbytes; ++b)
-                for (int v = 0; v < 256; ++v)
-                    for (int k = 0; k < 8; ++k) {
-                        const int t = 8 * b + k;
-                        if ((v >> k & 1) && t < hg.nterms) {
-                            pt.tre[b][v] += hg.cre[t];
-                            pt.tim[b][v] += hg.cim[t];
-                        }
-                    }
-            // per bit: the coefficient sum of the terms containing it and the table bytes they use
-            bool cim = false;
-            for (int t = 0; t < hg.nterms; ++t) cim = cim || hg.cim[t] != 0.0;
-            pt.incremental = 1;
-            for (int i = 0; i < 64; ++i) {
-                uint32_t list = 0xffffffffu;
-                int nbk = 0;
-                for (int t = 0; t < hg.nterms; ++t)
-                    if (hg.zm[t] >> i & 1) {
-                        pt.cb_re[i] += hg.cre[t];
-                        pt.cb_im[i] += hg.cim[t];
-                    }
-                for (int b = 0; b < pt.nbytes; ++b)
-                    if ((pt.col[i][b >> 2] >> (8 * (b & 3))) & 0xffu) {
-                        if (nbk < 4) list = (list & ~(0xffu << (8 * nbk))) | (uint32_t(b) << (8 * nbk));
-                        ++nbk;
-                    }
-                if (nbk > 4) pt.incremental = 0;
-                pt.bbytes[i] = list;
-            }
-            if (cudaMemcpyAsync(dpt, &pt, sizeof pt, cudaMemcpyHostToDevice, st) != cudaSuccess)
+            if (cudaMemcpyAsync(dpt, &w, sizeof w, cudaMemcpyHostToDevice, st) != cudaSuccess)
                 return cuda_fail("expect upload", err, errlen);
-            const int blog = std::min(12, c.n - 12);
-            nblk = 1 << blog;
-            const int klog = c.n - blog - 8;
-            const size_t dsm = size_t(pt.nbytes) * 256 * 2 * (c.dt == QS_C64 ? sizeof(float) : sizeof(double));
-            const int nw = hg.nterms <= 32 ? 1 : hg.nterms <= 64 ? 2 : 4;
+            const WhtTerms *dw = dpt;
+            const uint64_t ntiles = 1ull << (c.n - kWhtTileLog - w.pair);
+            const bool cplx = hg.xm != 0;
             if (c.dt == QS_C64)
-                rc_launch = launch_parity<float>((const float2 *)c.amp, hg.xm, klog, dpt, part, nblk, dsm, nw, cim, st);
+                nblk = launch_wht<float>((const float2 *)c.amp, c.n, dw, cplx, ntiles, part, st);
             else
-                rc_launch = launch_parity<double>((const double2 *)c.amp, hg.xm, klog, dpt, part, nblk, dsm, nw, cim, st);
+                nblk = launch_wht<double>((const double2 *)c.amp, c.n, dw, cplx, ntiles, part, st);
         } else {
             if (cudaMemcpyAsync(dgrp, &hg, sizeof(TermGroup), cudaMemcpyHostToDevice, st) != cudaSuccess)
                 return cuda_fail("expect upload", err, errlen);

@@ -337,16 +337,23 @@ def test_host_fault_injection_paths(monkeypatch):
 @pytest.mark.parametrize("dtype", [qs.QS_C64, qs.QS_C128])
 @pytest.mark.parametrize("n", [16, 19])
 def test_expectation_many_terms_per_x_mask(dtype, n):
-    """Groups of 8..128 Z strings per X mask take the parity-table kernel, larger groups the
-    per-term loop; both against the oracle on a random (circuit-prepared) state."""
+    """Groups of four or more Z strings per X mask take the Walsh-Hadamard tile kernel: X mask
+    zero, inside the 1024-amplitude tile (even and odd), above it (paired tiles, with and
+    without low bits); smaller groups take the per-term loop.  Against the oracle on a random
+    (circuit-prepared) state."""
     rng = W.SplitMix64(300 + n)
     gates = W.layered(n, 3, 77) + W.vqe_circuit(n, 2, 78)
     want = ref(n, gates)
-    terms = []
-    for xm, count in ((0, 40), (0b101 << 3, 9), (1 << (n - 1), 130), (0b11, 3)):
+    terms, by_group = [], []
+    groups = ((0, 40), (0b101 << 3, 9), (1 << (n - 1), 130), (0b11, 3), (0b1001, 12),
+              ((1 << (n - 2)) | 0b1, 20), ((1 << 12) | (1 << 10) | 0b110, 7))
+    for xm, count in groups:
+        grp = []
         for _ in range(count):
             zm = rng.next_u64() & ((1 << n) - 1)
-            terms.append((rng.angle() - 3.0, xm, zm))
+            grp.append((rng.angle() - 3.0, xm, zm))
+        by_group.append(grp)
+        terms += grp
     s = qs.State(n, dtype)
     try:
         s.apply(gates, qs.options(dtype=dtype))
@@ -354,5 +361,12 @@ def test_expectation_many_terms_per_x_mask(dtype, n):
         w = oracle.expect_pauli(want, n, terms)
         tol = (1e-9 if dtype == qs.QS_C128 else 2e-4) * len(terms)
         assert abs(e.real - w.real) <= tol and abs(e.imag - w.imag) <= tol
+        # each group alone, against the oracle on the device's own amplitudes (kernel arithmetic only)
+        mine = s.amplitudes().astype(np.complex128)
+        for grp in by_group:
+            e = s.expect(grp)
+            w = oracle.expect_pauli(mine, n, grp)
+            tol = (1e-12 if dtype == qs.QS_C128 else 2e-6) * sum(abs(c) for c, _, _ in grp)
+            assert abs(e.real - w.real) <= tol and abs(e.imag - w.imag) <= tol, grp[0][1]
     finally:
         s.close()
