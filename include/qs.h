@@ -260,7 +260,8 @@ qs_status qs_probs_noalloc(const void *dev_amp, int n, qs_dtype dt, const int *q
  * random numbers; the library draws none), host_out[k] receives the smallest logical index x
  * whose running weight sum_{y <= x} |a_y|^2 exceeds u[k] ||psi||^2 (inverse transform sampling,
  * in logical qubit order).  shots <= 2^28.  QS_EINVAL for a u outside [0, 1) or a zero state.
- * Synchronises; one read of the state plus one 2^12-amplitude block per shot. */
+ * Synchronises; one read of the state plus one 2^8-amplitude block per shot.  Scratch: 2^(n-4)
+ * bytes of block prefixes, held by the state. */
 qs_status qs_sample(qs_state *s, const double *u, size_t shots, uint64_t *host_out);
 
 /* host_out[0] = Re sum_t coeff_t <psi|P_t|psi>, host_out[1] = its imaginary part (zero up to

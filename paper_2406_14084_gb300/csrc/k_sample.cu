@@ -8,8 +8,9 @@
 //   2. scan_chunks_kernel / scan_tops_kernel / add_tops_kernel: exclusive prefix of the block
 //      sums (chunks of 1024 in shared memory, then the chunk totals in one block, then the
 //      offsets added back), so P[j] is the weight before block j and P[M] the total;
-//   3. sample_kernel: one warp per shot finds the block by binary search over P and then the
-//      index inside the block with warp-wide inclusive scans over runs of 32 amplitudes.
+//   3. sample_kernel: one warp per shot finds the block by binary search over P, loads the
+//      block's amplitudes at once and finds the index inside it with warp-wide inclusive scans
+//      over runs of 32 amplitudes.
 #include <cuda_runtime.h>
 
 #include <cstdio>
@@ -19,7 +20,10 @@
 namespace qs {
 namespace {
 
-constexpr int kBlockLog = 12;  // 4096 amplitudes per block
+// 256 amplitudes per block: a shot then reads one block (eight loads per lane, all in flight at
+// once) after a binary search over the 2^(n-8) block prefixes, which stay in L2 up to 32 qubits
+constexpr int kBlockLog = 8;
+constexpr int kLoads = (1 << kBlockLog) / 32;  // amplitudes per lane in one block
 constexpr int kChunk = 1024;   // block sums scanned per CTA
 
 template <typename R> struct Cx;
@@ -58,8 +62,15 @@ __global__ void block_sums_kernel(const typename Cx<R>::T *__restrict__ a, uint6
     const int lane = threadIdx.x & 31;
     if (w >= nblocks) return;
     const uint64_t base = w << blog, len = uint64_t(1) << blog;
+    typename Cx<R>::T v[kLoads];
+#pragma unroll
+    for (int c = 0; c < kLoads; ++c) {
+        const uint64_t i = uint64_t(c) * 32 + lane;
+        v[c] = i < len ? a[base + i] : typename Cx<R>::T{};
+    }
     double s = 0.0;
-    for (uint64_t i = lane; i < len; i += 32) s += weight(a[base + i]);
+#pragma unroll
+    for (int c = 0; c < kLoads; ++c) s += weight(v[c]);
     s = warp_sum(s);
     if (lane == 0) S[w] = s;
 }
@@ -136,15 +147,22 @@ __global__ void sample_kernel(const typename Cx<R>::T *__restrict__ a, int blog,
         else hi = mid - 1;
     }
     const uint64_t j = lo, base = j << blog, len = uint64_t(1) << blog;
+    double w[kLoads];  // the whole block, loaded at once; zero weight past its end (n < 8)
+#pragma unroll
+    for (int c = 0; c < kLoads; ++c) {
+        const uint64_t i = uint64_t(c) * 32 + lane;
+        w[c] = i < len ? weight(a[base + i]) : 0.0;
+    }
     double run = P[j];
     uint64_t found = ~uint64_t(0), last_nz = base;
-    for (uint64_t c = 0; c < len && found == ~uint64_t(0); c += 32) {
-        const double w = (c + lane < len) ? weight(a[base + c + lane]) : 0.0;  // blocks < 32 when n < 5
-        const double inc = warp_incl_scan(w, lane);
+#pragma unroll
+    for (int c = 0; c < kLoads; ++c) {
+        if (found != ~uint64_t(0)) break;  // warp-uniform
+        const double inc = warp_incl_scan(w[c], lane);
         const unsigned hit = __ballot_sync(0xffffffffu, run + inc > t);
-        const unsigned nz = __ballot_sync(0xffffffffu, w > 0.0);
-        if (nz) last_nz = base + c + 31 - __clz(nz);
-        if (hit) found = base + c + __ffs(hit) - 1;
+        const unsigned nz = __ballot_sync(0xffffffffu, w[c] > 0.0);
+        if (nz) last_nz = base + uint64_t(c) * 32 + 31 - __clz(nz);
+        if (hit) found = base + uint64_t(c) * 32 + __ffs(hit) - 1;
         run += __shfl_sync(0xffffffffu, inc, 31);
     }
     // rounding can leave t at or past this block's end: the last outcome of positive weight
