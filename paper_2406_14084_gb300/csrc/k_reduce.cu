@@ -389,15 +389,18 @@ __global__ void __launch_bounds__(kRedThreads) probs_small_kernel(const typename
 #pragma unroll
     for (int j = 0; j < Q; ++j) pos[j] = (w[j >> 2] >> (8 * (j & 3))) & 0xff;
     // complex64: FP32 partial sums of at most 32 amplitudes per bin, then FP64 (the FP64 pipe
-    // is 1/64 of the FP32 rate on this part); complex128: FP64 throughout
+    // is 1/64 of the FP32 rate on this part); with at most 8 bins, 32 of those partials are first
+    // summed in FP32 (converting every one kept the FP64 pipe 40 % busy on 3-qubit marginals;
+    // 32 bins would not fit the second level in registers); complex128: FP64 throughout
+    constexpr bool kTwoLevel = M <= 8;
     double acc[M];
-    R part[M];
+    R part[M], part2[M];
 #pragma unroll
     for (int b = 0; b < M; ++b) {
         acc[b] = 0.0;
-        part[b] = R(0);
+        part[b] = part2[b] = R(0);
     }
-    int cnt = 0;
+    int cnt = 0, cnt2 = 0;
     const uint64_t per = (N + gridDim.x - 1) / gridDim.x;
     const uint64_t lo = per * blockIdx.x;
     const uint64_t hi = lo + per < N ? lo + per : N;
@@ -429,14 +432,22 @@ __global__ void __launch_bounds__(kRedThreads) probs_small_kernel(const typename
         if (sizeof(R) == 4 && (cnt += U) >= 32) {
 #pragma unroll
             for (int b = 0; b < M; ++b) {
-                acc[b] += (double)part[b];
+                part2[b] += part[b];
                 part[b] = R(0);
             }
             cnt = 0;
+            if (!kTwoLevel || ++cnt2 == 32) {
+#pragma unroll
+                for (int b = 0; b < M; ++b) {
+                    acc[b] += (double)part2[b];
+                    part2[b] = R(0);
+                }
+                cnt2 = 0;
+            }
         }
     }
 #pragma unroll
-    for (int b = 0; b < M; ++b) acc[b] += (double)part[b];
+    for (int b = 0; b < M; ++b) acc[b] += (double)part[b] + (double)part2[b];
     const int lane = threadIdx.x & 31;
 #pragma unroll
     for (int b = 0; b < M; ++b) {

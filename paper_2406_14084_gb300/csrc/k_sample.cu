@@ -3,8 +3,8 @@
 // For caller-supplied uniforms u_k in [0, 1) the outcome of shot k is the smallest index x whose
 // running weight C(x) = sum_{y <= x} |a_y|^2 exceeds u_k * C(2^n - 1) (inverse transform).  The
 // state is cut into blocks of 2^kBlockLog amplitudes:
-//   1. block_sums_kernel: one warp per block sums |a|^2 in FP64 (fixed order: each lane a
-//      strided run, then a shuffle tree);
+//   1. block_sums_kernel: one warp per block sums |a|^2 (fixed order: each lane a strided run,
+//      then a shuffle tree) in FP64, or for complex64 in float-float pairs (~48 bits);
 //   2. scan_chunks_kernel / scan_tops_kernel / add_tops_kernel: exclusive prefix of the block
 //      sums (chunks of 1024 in shared memory, then the chunk totals in one block, then the
 //      offsets added back), so P[j] is the weight before block j and P[M] the total;
@@ -54,6 +54,30 @@ __device__ __forceinline__ double warp_incl_scan(double v, int lane)
     return v;
 }
 
+// Float-float (unevaluated hi + lo pair) arithmetic for complex64 block sums, so that the sums
+// keep about 48 bits without the FP64 pipe (1/64 of the FP32 rate on this part).  Error-free
+// transformations: Knuth's TwoSum and the FMA form of Dekker's TwoProduct; the _rn intrinsics
+// keep the compiler from contracting or reordering them.
+__device__ __forceinline__ void ff_add(float &hi, float &lo, float bh, float bl)
+{
+    const float s = __fadd_rn(hi, bh);
+    const float bb = __fsub_rn(s, hi);
+    float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(bh, bb));
+    e = __fadd_rn(e, __fadd_rn(lo, bl));
+    hi = __fadd_rn(s, e);  // renormalise (|s| >= |e|)
+    lo = __fsub_rn(e, __fsub_rn(hi, s));
+}
+
+// |v|^2 of a complex64 amplitude as a float-float pair (each square is exact as a pair).
+__device__ __forceinline__ void ff_weight(const float2 &v, float &hi, float &lo)
+{
+    const float px = __fmul_rn(v.x, v.x), py = __fmul_rn(v.y, v.y);
+    const float ex = __fmaf_rn(v.x, v.x, -px), ey = __fmaf_rn(v.y, v.y, -py);
+    hi = px;
+    lo = ex;
+    ff_add(hi, lo, py, ey);
+}
+
 template <typename R>
 __global__ void block_sums_kernel(const typename Cx<R>::T *__restrict__ a, uint64_t nblocks, int blog,
                                   double *__restrict__ S)
@@ -68,11 +92,27 @@ __global__ void block_sums_kernel(const typename Cx<R>::T *__restrict__ a, uint6
         const uint64_t i = uint64_t(c) * 32 + lane;
         v[c] = i < len ? a[base + i] : typename Cx<R>::T{};
     }
-    double s = 0.0;
+    if constexpr (sizeof(R) == 4) {
+        float hi = 0.f, lo = 0.f;
 #pragma unroll
-    for (int c = 0; c < kLoads; ++c) s += weight(v[c]);
-    s = warp_sum(s);
-    if (lane == 0) S[w] = s;
+        for (int c = 0; c < kLoads; ++c) {
+            float wh, wl;
+            ff_weight(v[c], wh, wl);
+            ff_add(hi, lo, wh, wl);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float oh = __shfl_xor_sync(0xffffffffu, hi, o), ol = __shfl_xor_sync(0xffffffffu, lo, o);
+            ff_add(hi, lo, oh, ol);
+        }
+        if (lane == 0) S[w] = (double)hi + (double)lo;
+    } else {
+        double s = 0.0;
+#pragma unroll
+        for (int c = 0; c < kLoads; ++c) s += weight(v[c]);
+        s = warp_sum(s);
+        if (lane == 0) S[w] = s;
+    }
 }
 
 // Exclusive prefix of S within chunks of kChunk; chunk totals to T.
