@@ -346,7 +346,8 @@ def test_expectation_many_terms_per_x_mask(dtype, n):
     want = ref(n, gates)
     terms, by_group = [], []
     groups = ((0, 40), (0b101 << 3, 9), (1 << (n - 1), 130), (0b11, 3), (0b1001, 12),
-              ((1 << (n - 2)) | 0b1, 20), ((1 << 12) | (1 << 10) | 0b110, 7))
+              ((1 << (n - 2)) | 0b1, 20), ((1 << 12) | (1 << 10) | 0b110, 7),
+              (0b110 << 9, 300))  # 300 terms: split into groups of 256 and 44
     for xm, count in groups:
         grp = []
         for _ in range(count):

@@ -27,7 +27,7 @@ def away_from_steps(a, u, rel=1e-12):
 
 
 @pytest.mark.parametrize("dtype", [qs.QS_C64, qs.QS_C128])
-@pytest.mark.parametrize("n", [1, 3, 10, 14, 17])
+@pytest.mark.parametrize("n", [1, 3, 7, 8, 9, 10, 14, 17])  # 8 = one 256-amplitude block
 def test_sample_matches_oracle_inverse_transform(dtype, n):
     gates = W.random_circuit(n, 60, 900 + n) if n > 1 else [Gate("U3", (0,), (), (0.4, 0.2, 0.1))]
     u = np.random.default_rng(n).random(3000)
