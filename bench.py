@@ -51,7 +51,9 @@ WORKLOADS = {
     "qaoa31_c128": dict(n=31, dtype="c128", kind="qaoa", p=5, seed=1006),
     "qft31_c128": dict(n=31, dtype="c128", kind="qft", seed=1006),
     "gatesweep30_c128": dict(n=30, dtype="c128", kind="gatesweep", reps=2, seed=1007),
+    "gatesweep30_c64": dict(n=30, dtype="c64", kind="gatesweep", reps=2, seed=1007),
     "hsweep_c128": dict(n=33, dtype="c128", kind="hsweep", seed=1008),
+    "hsweep_c64": dict(n=33, dtype="c64", kind="hsweep", seed=1008),
     "learned32_c128": dict(n=32, dtype="c128", kind="learned", depth=80, seed=1005),
     "learned28_c128": dict(n=28, dtype="c128", kind="learned", depth=80, seed=1005),
 }
@@ -490,6 +492,7 @@ def run_gate_sweeps(args, w):
                     row[mode + "_gates_per_s"] = len(g) / (ms / 1e3) if ms > 0 else None
                     if mode == "gate_by_gate" and ms > 0:
                         row["gate_by_gate_gbs"] = len(g) * 2.0 * (1 << n) * s_amp / (ms / 1e3) / 1e9
+                        row["gate_by_gate_frac_of_hbm"] = row["gate_by_gate_gbs"] / measured_peaks()["hbm_gbs"]
                     elif mode == "blocked" and ms > 0:
                         tot_g += len(g)
                         tot_ms += ms
@@ -509,6 +512,7 @@ def run_gate_sweeps(args, w):
                     row[mode + "_ms"] = ms
                     row[mode + "_passes"] = nst
                     row[mode + "_gbs"] = nst * 2.0 * (1 << n) * s_amp / (ms / 1e3) / 1e9
+                    row[mode + "_frac_of_hbm"] = row[mode + "_gbs"] / measured_peaks()["hbm_gbs"]
                     if mode == "blocked" and n == w["n"]:
                         tot_g, tot_ms = len(g), ms
                 rows[str(n)] = row
