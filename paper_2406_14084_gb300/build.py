@@ -37,7 +37,7 @@ def sources():
 
 
 def _headers_mtime() -> float:
-    hs = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".h")]
+    hs = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
     hs.append(os.path.join(INCLUDE, "qs.h"))
     return max(os.path.getmtime(h) for h in hs)
 

@@ -70,10 +70,7 @@ __device__ __forceinline__ I swz(I i)
 
 // ------------------------------------------------------------------ ops on an addressable array
 // `mem` is either the shared-memory slab (I = uint32_t, nbits = b) or the whole state in global
-// memory (I = uint64_t, nbits = n).  Work is split over threads [tid, tid + nthr, ...); the
-// 1-2 qubit, diagonal, phase and permutation ops take U disjoint groups per thread at a time and
-// issue all their loads before the first store, so several loads per thread are in flight (one
-// group at a time kept the gate-by-gate kernels at 30-50 % of HBM).
+// memory (I = uint64_t, nbits = n).  Work is split over threads [tid, tid + nthr, ...).
 
 template <typename C, int K, typename I, int SW>
 __device__ void op_dense(C *mem, int nbits, const DevOp &op, const C *__restrict__ coef,
@@ -96,28 +93,17 @@ __device__ void op_dense(C *mem, int nbits, const DevOp &op, const C *__restrict
         C m[D * D];
 #pragma unroll
         for (int e = 0; e < D * D; ++e) m[e] = M[e];
-        // U disjoint groups per thread: all their loads are issued before any store
-        constexpr int U = K == 1 ? 4 : 2;
-        for (I g0 = tid; g0 < ngroups; g0 += I(U) * nthr) {
-            I i0[U];
-            C v[U][D];
+        for (I g = tid; g < ngroups; g += nthr) {
+            const I i0 = insert_zeros<I>(g, op.ins, op.nins) | cm;
+            C v[D];
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const I g = g0 + I(u) * nthr;
-                i0[u] = insert_zeros<I>(g < ngroups ? g : g0, op.ins, op.nins) | cm;
+            for (int l = 0; l < D; ++l) v[l] = mem[swz<SW>(i0 | off[l])];
 #pragma unroll
-                for (int l = 0; l < D; ++l) v[u][l] = mem[swz<SW>(i0[u] | off[l])];
-            }
+            for (int r = 0; r < D; ++r) {
+                C acc = czero<C>();
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-                if (g0 + I(u) * nthr >= ngroups) break;  // past the end: loaded, never stored
-#pragma unroll
-                for (int r = 0; r < D; ++r) {
-                    C acc = czero<C>();
-#pragma unroll
-                    for (int l = 0; l < D; ++l) acc = cmac(m[r * D + l], v[u][l], acc);
-                    mem[swz<SW>(i0[u] | off[r])] = acc;
-                }
+                for (int l = 0; l < D; ++l) acc = cmac(m[r * D + l], v[l], acc);
+                mem[swz<SW>(i0 | off[r])] = acc;
             }
         }
     } else {
@@ -144,23 +130,11 @@ __device__ void op_diag(C *mem, int nbits, const DevOp &op, const C *__restrict_
     const I ngroups = I(1) << (nbits - op.nins);
     const I cm = (I)op.cmask;
     const int k = op.k;
-    constexpr int U = 4;  // disjoint amplitudes per thread, loads first
-    for (I g0 = tid; g0 < ngroups; g0 += I(U) * nthr) {
-        I i[U];
-        C v[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const I g = g0 + I(u) * nthr;
-            i[u] = insert_zeros<I>(g < ngroups ? g : g0, op.ins, op.nins) | cm;
-            v[u] = mem[swz<SW>(i[u])];
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            if (g0 + I(u) * nthr >= ngroups) break;
-            uint32_t idx = 0;
-            for (int j = 0; j < k; ++j) idx |= uint32_t((i[u] >> op.t[j]) & 1) << j;
-            mem[swz<SW>(i[u])] = cmul(__ldg(&table[idx]), v[u]);
-        }
+    for (I g = tid; g < ngroups; g += nthr) {
+        const I i = insert_zeros<I>(g, op.ins, op.nins) | cm;
+        uint32_t idx = 0;
+        for (int j = 0; j < k; ++j) idx |= uint32_t((i >> op.t[j]) & 1) << j;
+        mem[swz<SW>(i)] = cmul(__ldg(&table[idx]), mem[swz<SW>(i)]);
     }
 }
 
@@ -169,23 +143,11 @@ __device__ void op_permx(C *mem, int nbits, const DevOp &op, I tid, I nthr)
 {
     const I ngroups = I(1) << (nbits - op.nins);
     const I cm = (I)op.cmask, bit = I(1) << op.t[0];
-    constexpr int U = 4;
-    for (I g0 = tid; g0 < ngroups; g0 += I(U) * nthr) {
-        I i0[U];
-        C a[U], b[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const I g = g0 + I(u) * nthr;
-            i0[u] = insert_zeros<I>(g < ngroups ? g : g0, op.ins, op.nins) | cm;
-            a[u] = mem[swz<SW>(i0[u])];
-            b[u] = mem[swz<SW>(i0[u] | bit)];
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            if (g0 + I(u) * nthr >= ngroups) break;
-            mem[swz<SW>(i0[u])] = b[u];
-            mem[swz<SW>(i0[u] | bit)] = a[u];
-        }
+    for (I g = tid; g < ngroups; g += nthr) {
+        const I i0 = insert_zeros<I>(g, op.ins, op.nins) | cm;
+        const C a = mem[swz<SW>(i0)], b = mem[swz<SW>(i0 | bit)];
+        mem[swz<SW>(i0)] = b;
+        mem[swz<SW>(i0 | bit)] = a;
     }
 }
 
@@ -194,23 +156,11 @@ __device__ void op_swap(C *mem, int nbits, const DevOp &op, I tid, I nthr)
 {
     const I ngroups = I(1) << (nbits - op.nins);
     const I cm = (I)op.cmask, b0 = I(1) << op.t[0], b1 = I(1) << op.t[1];
-    constexpr int U = 4;
-    for (I g0 = tid; g0 < ngroups; g0 += I(U) * nthr) {
-        I i0[U];
-        C a[U], b[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const I g = g0 + I(u) * nthr;
-            i0[u] = insert_zeros<I>(g < ngroups ? g : g0, op.ins, op.nins) | cm;
-            a[u] = mem[swz<SW>(i0[u] | b0)];
-            b[u] = mem[swz<SW>(i0[u] | b1)];
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            if (g0 + I(u) * nthr >= ngroups) break;
-            mem[swz<SW>(i0[u] | b0)] = b[u];
-            mem[swz<SW>(i0[u] | b1)] = a[u];
-        }
+    for (I g = tid; g < ngroups; g += nthr) {
+        const I i0 = insert_zeros<I>(g, op.ins, op.nins) | cm;
+        const C a = mem[swz<SW>(i0 | b0)], b = mem[swz<SW>(i0 | b1)];
+        mem[swz<SW>(i0 | b0)] = b;
+        mem[swz<SW>(i0 | b1)] = a;
     }
 }
 
@@ -221,21 +171,9 @@ __device__ void op_phase(C *mem, int nbits, const DevOp &op, const C *__restrict
     const I ngroups = I(1) << (nbits - op.nins);
     const I cm = (I)op.cmask;
     const C ph = coef[op.mat];
-    constexpr int U = 4;
-    for (I g0 = tid; g0 < ngroups; g0 += I(U) * nthr) {
-        I i[U];
-        C v[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const I g = g0 + I(u) * nthr;
-            i[u] = insert_zeros<I>(g < ngroups ? g : g0, op.ins, op.nins) | cm;
-            v[u] = mem[swz<SW>(i[u])];
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            if (g0 + I(u) * nthr >= ngroups) break;
-            mem[swz<SW>(i[u])] = cmul(ph, v[u]);
-        }
+    for (I g = tid; g < ngroups; g += nthr) {
+        const I i = insert_zeros<I>(g, op.ins, op.nins) | cm;
+        mem[swz<SW>(i)] = cmul(ph, mem[swz<SW>(i)]);
     }
 }
 

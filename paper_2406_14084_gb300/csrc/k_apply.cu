@@ -5,7 +5,7 @@
 
 #include <cstdio>
 
-#include "dev_common.cuh"
+#include "op_global.cuh"
 #include "qs_internal.h"
 
 namespace qs {
@@ -22,7 +22,7 @@ __global__ void __launch_bounds__(256) unblocked_kernel(typename Cx<R>::T *__res
     __syncthreads();
     const uint64_t tid = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     const uint64_t nthr = uint64_t(gridDim.x) * blockDim.x;
-    apply_op<C, uint64_t, 0>(state, n, op, coef, 0u, tid, nthr);
+    apply_op_global<C, uint64_t, 0>(state, n, op, coef, 0u, tid, nthr);
 }
 
 template <typename R>
