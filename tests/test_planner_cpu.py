@@ -102,6 +102,20 @@ def test_gather_plans_match_oracle(fuse, dtype):
     assert info["input_gates"] == len(gates)
 
 
+@pytest.mark.parametrize("slab,seg,narrow", [(5, 1, 0), (6, 3, 1), (8, 2, 0), (8, 5, 1), (9, 4, 0), (10, 6, 1)])
+@pytest.mark.parametrize("dtype", [qs.QS_C64, qs.QS_C128])
+def test_slab_segment_and_stage_width_grid(slab, seg, narrow, dtype):
+    """Gather plans over a grid of slab sizes, contiguous segment bits and both register-stage
+    widths the kernels are built for (5 / 4 bits for complex64, 4 / 3 for complex128)."""
+    n = 10
+    stage = (5 if dtype == qs.QS_C64 else 4) - narrow
+    gates = mixed_circuit(n, 140, 6100 + 10 * slab + seg)
+    info, stats = check_plan(gates, n, qs.options(fuse_width=3, slab_bits=slab, seg_bits=seg,
+                                                  stage_bits=stage, dtype=dtype))
+    assert stats["max_b"] <= slab
+    assert info["stage_bits"] == stage and info["input_gates"] == len(gates)
+
+
 @pytest.mark.parametrize("slab", [4, 5, 7])
 def test_lowblock_remap_plans_match_oracle(slab):
     n = 10
