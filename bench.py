@@ -1,9 +1,9 @@
 """Benchmark: apply a fused, slab-blocked circuit to a full state vector on one GB300.
 
-Default workload (the plain method at scale): a 34-qubit complex64 layered random circuit of
-depth 40 (U3 on every qubit, then CZ on alternating neighbour pairs; 2,020 gates), seeded
-synthetic input standing in for the paper's generated benchmark circuits.  Other workloads:
---workload qft32_c128 | layered32_c128 | config1.
+Default workload (the plain method at scale, at the paper's FP64 precision): the quantum Fourier
+transform of a seeded random basis state on 32 qubits, complex128 (64 GiB state; 32 H + 496 CP
+gates), seeded synthetic input standing in for the paper's generated benchmark circuits.  Other
+workloads: --workload layered32_c128 | layered34_c64 | precision33_c64 | batch1024_c64 | ...
 
 One step = qs_apply_plan of the whole circuit on the resident state (every plan step: slab
 passes, remaps).  `value` = input gates / device time of the timed steps (CUDA events on the
@@ -12,8 +12,14 @@ state's stream, W warm-up steps first, barrier + synchronize on both sides, max 
 qs_apply_circuit (host gate list: planning and upload inside the timed region) +
 qs_expect_pauli_sum read back to the host.
 
---impl reference runs the FP64 CPU oracle on the host cores on a bounded sample of the same
-workload (a smaller state of the same circuit family, scaled by the state size).
+`forms` (default workload, one rank): the other configurations measured once each in the same
+run on the same GPU -- the 32-qubit complex128 layered circuit; tensor-core against plain form
+(33-qubit complex64, depth 60) with each mode's fidelity against the FP64 path; batched against
+per-circuit form (1024 ansatz circuits); learned against greedy planner.
+
+`cpu_baseline`: the FP64 CPU oracle on the machine's host cores, single-thread and OpenMP, on the
+first gates of the same circuit at the bench's qubit count when host memory allows it.
+--impl reference runs the same oracle as the reference arm.
 
 Multi-GPU: replicas only (the path has no exchange step on one-GPU machines); each rank runs the
 full workload and value = ranks x gates / max time.
@@ -34,6 +40,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 HBM_NOMINAL_GBS = 8000.0
+DEFAULT_WORKLOAD = "qft32_c128"
 WORKLOADS = {
     "layered34_c64": dict(n=34, dtype="c64", kind="layered", depth=40, seed=1002),
     "layered32_c128": dict(n=32, dtype="c128", kind="layered", depth=40, seed=1002),
@@ -116,16 +123,18 @@ def circuit_flops_per_amp(gates) -> float:
 
 
 def measured_traffic(n: int, dtype: str):
-    """DRAM bytes per slab-pass launch from the committed ncu summary, scaled by 2^(n - n_capture)
-    (every pass streams the whole state once); None if the kernel sources changed since."""
+    """DRAM bytes per slab-pass launch from the committed ncu summary of that precision, scaled
+    by 2^(n - n_capture) (every pass streams the whole state once); None if the kernel sources
+    changed since."""
     p = os.path.join(ROOT, "profiles", "slab_pass_traffic.json")
     if not os.path.exists(p):
         return None
     with open(p) as f:
-        t = json.load(f)
-    if t.get("source_hash") != slab_kernel_hash() or t.get("dtype") != dtype:
-        return None
-    return t["dram_bytes_per_launch"] * 2.0 ** (n - t["n"])
+        doc = json.load(f)
+    for t in doc.get("captures", [doc]):
+        if t.get("dtype") == dtype and t.get("source_hash") == slab_kernel_hash():
+            return t["dram_bytes_per_launch"] * 2.0 ** (n - t["n"])
+    return None
 
 
 def measured_peaks():
@@ -217,34 +226,100 @@ def dist_env():
 
 # ----------------------------------------------------------------------------- CPU oracle leg
 
-def oracle_sample(w, budget_s: float = 15.0):
-    """Time the FP64 oracle on a smaller state of the same circuit family; return gates/s
-    scaled to the full state size (work per gate is proportional to 2^n)."""
-    import numpy as np
+def host_info():
+    """CPU model, usable cores and host memory of this machine (read from /proc and lscpu)."""
+    info = {"nproc": len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()}
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.startswith("Model name:"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if model is None:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for ln in f:
+                    if ln.lower().startswith(("model name", "cpu part")):
+                        model = ln.split(":", 1)[1].strip()
+                        break
+        except OSError:
+            pass
+    info["cpu_model"] = model
+    try:
+        mem = {}
+        with open("/proc/meminfo") as f:
+            for ln in f:
+                k, v = ln.split(":", 1)
+                mem[k] = int(v.split()[0]) * 1024
+        info["host_ram_gb"] = mem.get("MemTotal", 0) / 1e9
+        info["mem_available_gb"] = mem.get("MemAvailable", 0) / 1e9
+    except OSError:
+        info["host_ram_gb"] = info["mem_available_gb"] = None
+    return info
 
+
+def oracle_qubits(n_full: int, hi: dict) -> int:
+    """Largest state (<= n_full qubits, complex128) the oracle may hold: at most 40 % of the
+    host's available memory, so the GPU process and the box keep ample headroom."""
+    avail = (hi.get("mem_available_gb") or 8.0) * 1e9
+    n = n_full
+    while n > 20 and (1 << n) * 16 > 0.4 * avail:
+        n -= 1
+    return n
+
+
+def oracle_timed_gates(n_s, gates, state, budget_s, max_gates):
+    """Apply gates one at a time from the start of the circuit until max_gates or the budget
+    is spent (at least one); returns (gates done, seconds)."""
+    import oracle
+
+    done, t0 = 0, time.perf_counter()
+    while done < min(max_gates, len(gates)):
+        oracle.apply_circuit(n_s, gates[done:done + 1], state)
+        done += 1
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    return done, time.perf_counter() - t0
+
+
+def oracle_sample(w, budget_s: float = 15.0):
+    """The FP64 oracle on the host cores, on the first gates of the same circuit (the whole
+    circuit's first 50 gates at most): single-thread, then OpenMP over every usable core, each
+    within half the budget.  The state has the bench's qubit count when host memory allows it;
+    otherwise the largest that fits, and gates/s is scaled by the state-size ratio (the work per
+    gate is proportional to 2^n).  Host GB/s counts one read and one write of the state per gate."""
     import oracle
 
     if w["kind"] == "batch":
         return oracle_sample_batch(w, budget_s)
 
+    hi = host_info()
     n_full = w["n"]
-    n_s = min(n_full, 25)
+    n_s = oracle_qubits(n_full, hi)
     gates, x0 = make_circuit(w, n_s)
     state = oracle.basis_state(n_s, x0 & ((1 << n_s) - 1))
-    oracle.apply_circuit(n_s, gates[:2], state)  # warm
-    done, t0 = 0, time.perf_counter()
-    i = 0
-    while time.perf_counter() - t0 < budget_s and i < len(gates):
-        chunk = gates[i:i + 8]
-        oracle.apply_circuit(n_s, chunk, state)
-        i += len(chunk)
-        done += len(chunk)
-    dt = time.perf_counter() - t0
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    rate = done / dt * (2.0 ** (n_s - n_full))
-    return {"value": rate, "unit": "gates/s", "cores": cores, "kind": "oracle",
-            "sample": f"first {done} gates of the same circuit family on a {n_s}-qubit complex128 "
-                      f"state in {dt:.1f} s, gates/s scaled by 2^({n_s}-{n_full})"}
+    scale = 2.0 ** (n_s - n_full)
+    gate_bytes = 2.0 * (1 << n_s) * 16
+    threads_all = int(hi["nproc"] or 1)
+    modes = {}
+    for name, threads, cap in (("single_thread", 1, 50), ("openmp", threads_all, 50)):
+        oracle.set_threads(threads)
+        done, dt = oracle_timed_gates(n_s, gates, state, budget_s / 2, cap)
+        per_gate = dt / done
+        modes[name] = {"threads": threads, "gates": done, "seconds": dt, "s_per_gate": per_gate,
+                       "gates_per_s": scale / per_gate, "host_gbs": gate_bytes / per_gate / 1e9}
+    oracle.set_threads(threads_all)
+    del state
+    omp = modes["openmp"]
+    return {"value": omp["gates_per_s"], "unit": "gates/s", "cores": threads_all, "kind": "oracle",
+            "sample": (f"first {omp['gates']} gates (OpenMP, {threads_all} threads) and first "
+                       f"{modes['single_thread']['gates']} (1 thread) of the same circuit on a "
+                       f"{n_s}-qubit complex128 state"
+                       + ("" if n_s == n_full else f", gates/s scaled by 2^({n_s}-{n_full})")),
+            "qubits": n_s, "dtype": "c128", "modes": modes, "host": hi}
 
 
 def oracle_sample_batch(w, budget_s: float):
@@ -269,6 +344,71 @@ def oracle_sample_batch(w, budget_s: float):
     return {"value": total_gates / est, "unit": "gates/s", "cores": cores, "kind": "oracle",
             "sample": f"{done_c} smallest circuits of the batch (with <H>) in {dt:.1f} s; rate of "
                       f"amplitude-gate updates scaled to all {len(circuits)} circuits"}
+
+
+def run_reference(args, w):
+    """The reference arm: the FP64 CPU oracle as it stands, on every usable host core.  Each
+    step is a bounded sample of the workload (the next gates of the circuit, continuing where
+    the previous step stopped, on one resident state), sized so that the K + W steps take a few
+    minutes in all; value = gates per second scaled to the workload's state size, ms_per_step =
+    the whole circuit's gate count at that rate."""
+    import oracle
+
+    if w["kind"] == "batch":
+        cpu = oracle_sample_batch(w, args.cpu_budget)
+        v = cpu["value"]
+        gates_full = sum(len(g) for _, g in __import__("paper_2406_14084_gb300.workloads",
+                                                         fromlist=["vqe_batch"]).vqe_batch(
+            w["count"], w["seed"], nmax=w.get("nmax", 24)))
+        ms = 1e3 * gates_full / v
+        return {"impl": "reference", "metric": "gates/s", "value": v, "unit": "gates/s", "n_gpus": args.gpus,
+                "steps": 1, "warmup": 0, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "c128", "data": "synthetic (seeded generator)",
+                "config": {"workload": args.workload}, "cpu_baseline": cpu,
+                "e2e": {"value": v, "unit": "gates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    hi = host_info()
+    n_full = w["n"]
+    n_s = oracle_qubits(n_full, hi)
+    gates, x0 = make_circuit(w, n_s)
+    full_gates = len(make_circuit(w)[0]) if n_s != n_full else len(gates)
+    threads = int(hi["nproc"] or 1)
+    oracle.set_threads(threads)
+    state = oracle.basis_state(n_s, x0 & ((1 << n_s) - 1))
+    scale = 2.0 ** (n_s - n_full)
+    per_step = max(1.0, min(args.cpu_budget, 150.0 / max(1, args.steps)))
+    pos = [0]
+
+    def step(budget, cap):
+        if pos[0] >= len(gates):
+            oracle.set_basis(state, n_s, x0 & ((1 << n_s) - 1))
+            pos[0] = 0
+        done, dt = oracle_timed_gates(n_s, gates[pos[0]:], state, budget, cap)
+        pos[0] += done
+        return done, dt
+
+    for _ in range(args.warmup):
+        step(0.0, 1)
+    tot_g, tot_s, step_s = 0, 0.0, []
+    for _ in range(args.steps):
+        d, dt = step(per_step, 10 ** 9)
+        tot_g += d
+        tot_s += dt
+        step_s.append(dt)
+    rate = tot_g / tot_s * scale
+    sample = (f"{args.steps} steps of about {per_step:.1f} s, each the next gates of the circuit "
+              f"({tot_g} gates in all) on a {n_s}-qubit complex128 state with {threads} OpenMP threads"
+              + ("" if n_s == n_full else f", gates/s scaled by 2^({n_s}-{n_full})"))
+    cpu = {"value": rate, "unit": "gates/s", "cores": threads, "kind": "oracle", "sample": sample,
+           "qubits": n_s, "dtype": "c128", "host": hi,
+           "host_gbs": 2.0 * (1 << n_s) * 16 * tot_g / tot_s / 1e9}
+    return {"impl": "reference", "metric": "gates/s", "value": rate, "unit": "gates/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * full_gates / rate,
+            "ms_per_step_basis": "the whole circuit's gates at the measured per-gate time",
+            "sample_ms_per_step": 1e3 * statistics.mean(step_s), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic (seeded generator)",
+            "config": {"workload": args.workload, "qubits": n_full, "gates": full_gates},
+            "cpu_baseline": cpu,
+            "e2e": {"value": rate, "unit": "gates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
 def run_batch(args, w):
@@ -574,6 +714,220 @@ def fidelity_vs_fp64_path(w, opts, n_copy=26):
             "max_abs_err": float(np.max(np.abs(got - want))), "norm_drift": float(ng - nw),
             "reference": "complex128 path of this library (FP64), same circuit"}
 
+# ----------------------------------------------------------------------------- forms
+
+def _timed_apply_ms(qs, torch, st, plan, stream, x0=0):
+    """One qs_apply_plan on a fresh start state, device time by CUDA events on the state's stream."""
+    qs.qs_set_basis(st.h, x0)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    qs.qs_apply_plan(st.h, plan)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def _plan_alu(qs, plan, n, ms, dtype):
+    flops = 2.0 * float(qs.qs_plan_features(plan)[:, 26].sum()) * (1 << n)
+    peak = ALU_PEAK_TFLOPS["c64" if dtype == qs.QS_C64 else "c128"]
+    return {"tflops": flops / (ms / 1e3) / 1e12, "frac_of_alu_peak": flops / (ms / 1e3) / 1e12 / peak}
+
+
+def form_layered32_c128(qs, torch):
+    """Config 2(ii): 32-qubit complex128 layered circuit of depth 40, greedy plan, one apply."""
+    w = WORKLOADS["layered32_c128"]
+    n, dtype = w["n"], qs.QS_C128
+    gates, x0 = make_circuit(w)
+    opts = qs.options(dtype=dtype)
+    plan = qs.qs_fuse(gates, n, opts)
+    info = qs.qs_plan_info_get(plan)
+    stream = torch.cuda.Stream()
+    with qs.State(n, dtype) as st:
+        qs.qs_set_stream(st.h, stream.cuda_stream)
+        ms = _timed_apply_ms(qs, torch, st, plan, stream, x0)
+        norm = qs.qs_norm2(st.h)
+    passes = info["passes"] + info["remaps"] + info["unblocked"]
+    gbs = passes * 2.0 * (1 << n) * 16 / (ms / 1e3) / 1e9
+    out = {"workload": "layered32_c128", "qubits": n, "gates": len(gates), "dtype": "c128",
+           "ms": ms, "gates_per_s": len(gates) / (ms / 1e3), "passes": passes,
+           "effective_hbm_gbs": gbs, "frac_of_hbm": gbs / measured_peaks()["hbm_gbs"],
+           "alu": _plan_alu(qs, plan, n, ms, dtype), "norm_after": norm,
+           "fidelity": fidelity_check(w, opts, dtype, n_small=20)}
+    qs.qs_plan_destroy(plan)
+    return out
+
+
+def form_tensor_cores(qs, torch):
+    """Config 3: 33-qubit complex64 layered depth 60; tensor-core plan (6-qubit blocks, BF16 x 3
+    split products) against the plain SIMT plan, one apply each; each mode's fidelity and max
+    |delta amp| against the FP64 path on the 26-qubit copy, and against the oracle at 20 qubits."""
+    w = WORKLOADS["precision33_c64"]
+    n, dtype = w["n"], qs.QS_C64
+    gates, x0 = make_circuit(w)
+    o_plain = qs.options(dtype=dtype)
+    modes = {"bf16x3": qs.QS_TC_BF16X3, "tf32x3": qs.QS_TC_TF32X3}
+    res = {"workload": "precision33_c64", "qubits": n, "gates": len(gates), "dtype": "c64", "modes": {}}
+    stream = torch.cuda.Stream()
+    p_plain = qs.qs_fuse(gates, n, o_plain)
+    with qs.State(n, dtype) as st:
+        qs.qs_set_stream(st.h, stream.cuda_stream)
+        ms_plain = _timed_apply_ms(qs, torch, st, p_plain, stream, x0)
+        res["plain"] = {"ms": ms_plain, "gates_per_s": len(gates) / (ms_plain / 1e3),
+                        "passes": qs.qs_plan_info_get(p_plain)["passes"]}
+        qs.qs_plan_destroy(p_plain)
+        for name, mode in modes.items():
+            o = qs.options(dtype=dtype, tc=mode)
+            try:
+                p = qs.qs_fuse(gates, n, o)
+            except qs.QsError as e:
+                res["modes"][name] = {"unsupported": str(e)}
+                continue
+            info = qs.qs_plan_info_get(p)
+            qs.qs_stats_reset(st.h)
+            ms = _timed_apply_ms(qs, torch, st, p, stream, x0)
+            stt = qs.qs_stats(st.h)
+            qs.qs_plan_destroy(p)
+            r = {"ms": ms, "gates_per_s": len(gates) / (ms / 1e3), "speedup_vs_plain": ms_plain / ms,
+                 "tc_gates": info["tc_gates"], "passes": info["passes"]}
+            if stt["tc_gates"]:
+                r["tc_launch_ms"] = stt["tc_ms"] / stt["tc_gates"]
+            r["fidelity_vs_fp64_path"] = fidelity_vs_fp64_path(w, o)
+            r["fidelity_vs_oracle"] = fidelity_check(w, o, dtype, n_small=20)
+            res["modes"][name] = r
+    return res
+
+
+def form_batch(qs, torch, dtype_name):
+    """Config 4: 1024 ansatz circuits in one persistent launch (autotuned, graph replay) against
+    the per-circuit form (plans built beforehand; per circuit: start state, qs_apply_plan,
+    qs_expect_pauli_sum), same GPU; max |delta <H>| between the two."""
+    import numpy as np
+
+    from paper_2406_14084_gb300 import workloads as W
+
+    w = WORKLOADS["batch1024_" + dtype_name]
+    dtype = qs.QS_C64 if dtype_name == "c64" else qs.QS_C128
+    circuits = W.vqe_batch(w["count"], w["seed"], nmax=w.get("nmax", 24))
+    H = W.zz_chain_hamiltonian(24)
+    ngates = sum(len(g) for _, g in circuits)
+    b = qs.qs_batch_create(circuits, qs.options(dtype=dtype, graph=1))
+    try:
+        chosen = qs.qs_batch_tune(b, H)
+        qs.qs_apply_batch(b, H, len(circuits))
+        res = qs.qs_apply_batch(b, H, len(circuits))
+        batch_ms = qs.qs_batch_info_get(b)["last_run_ms"]
+    finally:
+        qs.qs_batch_destroy(b)
+    plans = [qs.qs_fuse(g, m, qs.options(dtype=dtype)) for m, g in circuits]
+    states = {m: qs.State(m, dtype) for m in sorted({m for m, _ in circuits})}
+    Hs = {m: W.zz_chain_hamiltonian(m) for m in states}
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    plain = []
+    for (m, _), p in zip(circuits, plans):
+        st = states[m]
+        qs.qs_set_basis(st.h, 0)
+        qs.qs_apply_plan(st.h, p)
+        plain.append(qs.qs_expect_pauli_sum(st.h, Hs[m]).real)
+    plain_s = time.perf_counter() - t0
+    for p in plans:
+        qs.qs_plan_destroy(p)
+    for st in states.values():
+        st.close()
+    return {"workload": "batch1024_" + dtype_name, "circuits": len(circuits), "gates": ngates,
+            "dtype": dtype_name, "slab_bits": chosen,
+            "batched": {"ms": batch_ms, "gates_per_s": ngates / (batch_ms / 1e3)},
+            "per_circuit": {"ms": 1e3 * plain_s, "gates_per_s": ngates / plain_s},
+            "speedup_vs_per_circuit": 1e3 * plain_s / batch_ms,
+            "max_abs_diff_expect_H": float(np.max(np.abs(np.array(plain) - res)))}
+
+
+def form_learned(qs, torch, n):
+    """Config 5: learned planner against greedy on layered depth 80 and QFT, complex128.  Each
+    circuit: the greedy plan once; the learned plan three times (the first apply times the
+    model's pick, the second its greedy twin, the third runs what the judge kept).  Outputs of
+    the two plans compared on sampled amplitudes, and the learned plan against the oracle at
+    20 qubits."""
+    import numpy as np
+
+    import oracle
+    from paper_2406_14084_gb300 import costmodel
+    from paper_2406_14084_gb300 import workloads as W
+
+    dtype = qs.QS_C128
+    model = costmodel.load(os.path.join(ROOT, "paper_2406_14084_gb300", "data", "cost_model.npz"))
+    circuits = [("layered80", W.layered(n, 80, 1005)), ("qft", W.qft(n))]
+    stream = torch.cuda.Stream()
+    out = {"qubits": n, "dtype": "c128", "circuits": {}}
+    tot = {"greedy": 0.0, "judged": 0.0}
+    try:
+        with qs.State(n, dtype) as sg, qs.State(n, dtype) as sl:
+            for st in (sg, sl):
+                qs.qs_set_stream(st.h, stream.cuda_stream)
+            for name, g in circuits:
+                pg = qs.qs_fuse(g, n, qs.options(dtype=dtype))
+                pl = qs.qs_fuse_learned(g, n, qs.options(dtype=dtype), model)
+                info = qs.qs_plan_info_get(pl)
+                ms_g = _timed_apply_ms(qs, torch, sg, pg, stream)
+                ms_pick = _timed_apply_ms(qs, torch, sl, pl, stream)
+                ms_twin = _timed_apply_ms(qs, torch, sl, pl, stream)
+                ms_j = _timed_apply_ms(qs, torch, sl, pl, stream)
+                rng = np.random.default_rng(7)
+                worst = 0.0
+                for first in [0] + [int(v) * 4096 for v in rng.integers(0, (1 << n) // 4096, size=7)]:
+                    a = qs.qs_copy_to_host(sg.h, n, dtype, first, 4096)
+                    b = qs.qs_copy_to_host(sl.h, n, dtype, first, 4096)
+                    worst = max(worst, float(np.max(np.abs(a - b))))
+                small = W.layered(20, 80, 1005) if name == "layered80" else W.qft(20)
+                want = oracle.apply_circuit(20, small)
+                p22 = qs.qs_fuse_learned(small, 20, qs.options(dtype=dtype), model)
+                with qs.State(20, dtype) as s22:
+                    qs.qs_apply_plan(s22.h, p22)
+                    err22 = float(np.max(np.abs(s22.amplitudes() - want)))
+                qs.qs_plan_destroy(p22)
+                out["circuits"][name] = {
+                    "gates": len(g), "greedy_ms": ms_g, "model_pick_ms": ms_pick, "greedy_twin_ms": ms_twin,
+                    "judged_ms": ms_j, "gain_judged": ms_g / ms_j, "gain_model_pick": ms_g / ms_pick,
+                    "chosen": info["chosen"], "candidates": info["candidates"],
+                    "predicted_ms": info["predicted_ms"], "greedy_predicted_ms": info["greedy_predicted_ms"],
+                    "max_abs_diff_vs_greedy_sampled": worst, "max_abs_err_vs_oracle_20q": err22}
+                tot["greedy"] += ms_g
+                tot["judged"] += ms_j
+                qs.qs_plan_destroy(pg)
+                qs.qs_plan_destroy(pl)
+    finally:
+        qs.qs_model_destroy(model)
+    out["gain_judged_total"] = tot["greedy"] / tot["judged"]
+    return out
+
+
+def run_forms(args):
+    """Every other configuration, measured once on the same GPU in the same run."""
+    import torch
+
+    from paper_2406_14084_gb300 import qs
+
+    forms, t0 = {}, time.perf_counter()
+    jobs = [("layered32_c128", lambda: form_layered32_c128(qs, torch)),
+            ("tensor_cores_vs_plain", lambda: form_tensor_cores(qs, torch)),
+            ("batched_vs_per_circuit_c64", lambda: form_batch(qs, torch, "c64")),
+            ("batched_vs_per_circuit_c128", lambda: form_batch(qs, torch, "c128")),
+            ("learned_vs_greedy", lambda: form_learned(qs, torch, args.learned_n))]
+    for name, job in jobs:
+        if time.perf_counter() - t0 > args.forms_budget:
+            forms[name] = {"skipped": f"forms time budget of {args.forms_budget:.0f} s spent"}
+            continue
+        t1 = time.perf_counter()
+        try:
+            forms[name] = job()
+        except Exception as e:  # a form that fails is reported, not fatal to the bench line
+            forms[name] = {"error": f"{type(e).__name__}: {e}"}
+        forms[name]["wall_s"] = time.perf_counter() - t1
+        torch.cuda.synchronize()
+    return forms
+
+
 def run_gpu(args, w, ws, rank, local):
     import torch
 
@@ -677,6 +1031,22 @@ def run_gpu(args, w, ws, rank, local):
                    "frac": tc_tflops / peaks["bf16_tflops"], "kernel": "tc_bf16_kernel",
                    "peak_source": "BF16 dense, " + peaks["source"]}
     alu_peak = ALU_PEAK_TFLOPS["c64" if dtype == qs.QS_C64 else "c128"]
+    roof_alu = {"bound": "alu", "achieved": alu_tflops, "peak": alu_peak, "unit": "TFLOP/s",
+                "frac": alu_tflops / alu_peak, "traffic": traffic, "kernel": "slab_pass_kernel",
+                "avg_launch_ms": dom_ms,
+                "flops_per_launch": exec_flops_amp * (1 << n) / max(1, passes_per_step),
+                "algorithmic_flops_per_amp": exec_flops_amp,
+                "algorithmic_basis": "the fused plan's ops: 8 * 2^k flops per amplitude for a dense "
+                                     "k-qubit op, 4 for a real 2 x 2 rotation, 6 for a diagonal",
+                "circuit_flops_per_amp": algo_flops_amp,
+                "peak_source": "152 SMs x 2.07 GHz x (128 FP32 | 2 FP64) FMA/clk x 2 (unit counts "
+                               "and the maximum SM clock)"}
+    # the roofline that binds is the one whose floor (work / peak) is the larger: memory for a
+    # pass with little arithmetic, the FMA pipe of the state precision for a deep gate block
+    if tc_roof is None and roof_alu["frac"] > roof["frac"]:
+        roof, roof_other = roof_alu, roof
+    else:
+        roof_other = roof_alu
     norm = qs.qs_norm2(state.h)
     fidelity = None if args.no_fidelity else fidelity_check(w, opts, dtype)
     fidelity_fp64 = fidelity_vs_fp64_path(w, opts) if (opts.tc and not args.no_fidelity) else None
@@ -729,14 +1099,8 @@ def run_gpu(args, w, ws, rank, local):
         "fidelity_vs_fp64_path": fidelity_fp64,
         "tc": bool(opts.tc),
         "roofline": roof,
+        "roofline_other": roof_other,
         "roofline_tensor": tc_roof,
-        "roofline_alu": {"bound": "alu", "achieved": alu_tflops, "peak": alu_peak, "unit": "TFLOP/s",
-                         "frac": alu_tflops / alu_peak, "kernel": "slab_pass_kernel",
-                         "executed_flops_per_amp": exec_flops_amp,
-                         "circuit_algorithmic_flops_per_amp": algo_flops_amp,
-                         "circuit_algorithmic_tflops": algo_flops_amp * (1 << n) * args.steps
-                         / (pass_ms_total / 1e3) / 1e12,
-                         "peak_source": "152 SMs x 2.07 GHz x (128 FP32 | 2 FP64) FMA/clk x 2"},
         "clocks": clk,
         "gpu_launches": args.steps * nsteps,
         "e2e": e2e,
@@ -747,10 +1111,10 @@ def run_gpu(args, w, ws, rank, local):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)  # timed work about a minute at 34 qubits
+    ap.add_argument("--steps", type=int, default=10)  # about half a minute of timed work
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="layered34_c64", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--fuse", type=int, default=None)
     ap.add_argument("--slab-bits", type=int, default=0)
     ap.add_argument("--slab-mode", default="gather", choices=["gather", "remap"])
@@ -761,6 +1125,9 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--forms", default="auto", choices=["auto", "on", "off"])
+    ap.add_argument("--forms-budget", type=float, default=600.0)
+    ap.add_argument("--learned-n", type=int, default=30)
     args = ap.parse_args()
     ws, rank, local = dist_env()
     w = WORKLOADS[args.workload]
@@ -768,23 +1135,7 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        vals = []
-        for _ in range(args.warmup):
-            oracle_sample(w, budget_s=min(3.0, args.cpu_budget))
-        samples = [oracle_sample(w, budget_s=args.cpu_budget) for _ in range(args.steps)]
-        vals = [s["value"] for s in samples]
-        v = statistics.median(vals)
-        cpu = dict(samples[0])
-        cpu["value"] = v
-        print(json.dumps({
-            "impl": "reference", "metric": "gates/s", "value": v, "unit": "gates/s",
-            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1e3 * args.cpu_budget, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "c128", "data": "synthetic (seeded generator)",
-            "config": {"workload": args.workload, "qubits": w["n"]},
-            "cpu_baseline": cpu,
-            "e2e": {"value": v, "unit": "gates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-        }))
+        print(json.dumps(run_reference(args, w)))
         return
 
     if w["kind"] == "batch":
@@ -807,6 +1158,9 @@ def main():
         line = run_gpu(args, w, ws, rank, local)
     if line is None:
         return
+    if args.forms == "on" or (args.forms == "auto" and args.workload == DEFAULT_WORKLOAD and ws == 1
+                              and w["kind"] not in ("batch", "learned", "gatesweep", "hsweep", "readout")):
+        line["forms"] = run_forms(args)
     if not args.no_cpu_baseline and ws == 1 and w["kind"] not in ("gatesweep", "hsweep", "learned", "readout"):
         line["cpu_baseline"] = oracle_sample(w, budget_s=args.cpu_budget)
     print(json.dumps(line))

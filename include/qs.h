@@ -241,14 +241,19 @@ qs_status qs_probs(qs_state *s, const int *qubits, int nq, double *host_out);
  * synchronise or fail).  This entry point uses no allocation of any kind: its histogram lives
  * in one fixed device array of 2^14 doubles (128 KiB) that every GPU loading the library holds
  * until the process exits.
- *   dev_amp:   caller-owned device buffer of 2^n amplitudes of dt, read only; indices are
- *              physical (no qubit layout is applied), 16-byte aligned.
+ *   dev_amp:   caller-owned buffer of 2^n amplitudes of dt in device (or managed) memory of
+ *              the current device, read only; indices are physical (no qubit layout is
+ *              applied), 16-byte aligned.  A host pointer or another device's memory gives
+ *              QS_EINVAL before any launch (cudaPointerGetAttributes); the buffer's size cannot
+ *              be checked and must cover 2^n amplitudes.
  *   qubits:    nq distinct physical bit positions, 0 <= nq <= 14 (QS_EINVAL beyond that);
  *              host_out[m] (2^nq doubles, host) = probability that bit qubits[j] reads bit j
  *              of m.
  *   stream:    cudaStream_t to run on (NULL = legacy default stream); synchronised on return.
+ *              The call copies into pageable host memory and synchronises, so it may never run
+ *              while that stream is being captured: QS_EINVAL then.
  * The first call on each device looks up the array's device address (cudaGetSymbolAddress)
- * with that device current; make that first call before any stream capture.  Every call uses
+ * with that device current.  Every call uses
  * the same array and overwrites the previous call's histogram (the bins used are cleared
  * first), so calls that overlap on the GPU (different streams or host threads at once) race
  * and must be serialised by the caller. */
@@ -373,6 +378,9 @@ qs_status qs_model_info_get(const qs_model *m, qs_model_info *out);
  * input index first.  count must equal nparams.  set resets the Adam moments and step. */
 qs_status qs_model_get_params(const qs_model *m, float *host, size_t count);
 qs_status qs_model_set_params(qs_model *m, const float *host, size_t count);
+/* Adam's moment estimates m and v (Kingma & Ba, Algorithm 1), one per parameter in the order of
+ * qs_model_get_params; both are zero after create / set_params.  count must equal nparams. */
+qs_status qs_model_get_moments(const qs_model *m, float *mom, float *vel, size_t count);
 /* Standardisation: inputs x' = (x - mu) / sd per feature, targets t' = (t - ym) / ys. */
 qs_status qs_model_get_norm(const qs_model *m, float *mu, float *sd, float *ym, float *ys);
 qs_status qs_model_set_norm(qs_model *m, const float *mu, const float *sd, float ym, float ys);

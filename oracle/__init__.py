@@ -75,6 +75,9 @@ def lib():
             L.or_gate_matrix.argtypes = [ctypes.POINTER(_Gate), dp]
             L.or_init_basis.argtypes = [dp, ctypes.c_int, ctypes.c_uint64]
             L.or_init_basis.restype = None
+            L.or_set_threads.argtypes = [ctypes.c_int]
+            L.or_set_threads.restype = None
+            L.or_get_threads.argtypes = []
             L.or_remap.argtypes = [dp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                    ctypes.POINTER(ctypes.c_int)]
             L.or_norm2.argtypes = [dp, ctypes.c_int]
@@ -131,6 +134,13 @@ def basis_state(n: int, x: int = 0) -> np.ndarray:
     a = np.empty(1 << n, dtype=np.complex128)
     lib().or_init_basis(_dptr(a), n, x)
     return a
+
+
+def set_basis(state: np.ndarray, n: int, x: int = 0) -> np.ndarray:
+    """Overwrite ``state`` (2^n complex128) with the basis state |x>, in place."""
+    assert state.dtype == np.complex128 and state.shape == (1 << n,)
+    lib().or_init_basis(_dptr(state), n, x)
+    return state
 
 
 def apply_circuit(n: int, gates, state: np.ndarray | None = None) -> np.ndarray:
@@ -252,3 +262,12 @@ def adam_step(p, g, m, v, t, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
     for a in (p, g, m, v):
         assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
     lib().or_adam_step(_dptr(p), _dptr(g), _dptr(m), _dptr(v), p.size, t, lr, beta1, beta2, eps)
+
+
+def set_threads(t: int) -> None:
+    """Thread count of the oracle's OpenMP loops (results are identical at any count)."""
+    lib().or_set_threads(int(t))
+
+
+def get_threads() -> int:
+    return int(lib().or_get_threads())

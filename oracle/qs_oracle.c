@@ -31,6 +31,9 @@
 #include "qs_oracle.h"
 
 #include <complex.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
@@ -255,6 +258,26 @@ int or_apply_circuit(double *state, int n, const or_gate *gates, int ng)
         if (rc) return rc;
     }
     return 0;
+}
+
+/* Thread count of the OpenMP loops (1 when built without OpenMP).  Results do not depend on
+ * it: every loop iteration writes its own outputs. */
+void or_set_threads(int t)
+{
+#ifdef _OPENMP
+    if (t > 0) omp_set_num_threads(t);
+#else
+    (void)t;
+#endif
+}
+
+int or_get_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
 }
 
 void or_init_basis(double *state, int n, uint64_t x)

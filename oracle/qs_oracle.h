@@ -51,6 +51,8 @@ int or_gate_matrix(const or_gate *g, double *U);
 int or_apply_gate(double *state, int n, const or_gate *g);
 int or_apply_circuit(double *state, int n, const or_gate *gates, int ng);
 void or_init_basis(double *state, int n, uint64_t x);
+void or_set_threads(int t);
+int or_get_threads(void);
 int or_remap(double *state, int n, int k, const int *A, const int *B);
 double or_norm2(const double *state, int n);
 int or_probs(const double *state, int n, const int *q, int nq, double *out);

@@ -1019,6 +1019,29 @@ qs_status qs_probs_noalloc(const void *dev_amp, int n, qs_dtype dt, const int *q
         seen |= 1ull << q;
         phys[j] = q;
     }
+    // The buffer must be device (or managed) memory of the current device: a host pointer or
+    // another GPU's memory would make the kernel fault.  Neither query allocates.
+    int cur = 0;
+    if (cudaGetDevice(&cur) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(QS_ECUDA, "qs_probs_noalloc: no current CUDA device");
+    }
+    cudaPointerAttributes pa{};
+    if (cudaPointerGetAttributes(&pa, dev_amp) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(QS_EINVAL, "qs_probs_noalloc: dev_amp is not a CUDA device pointer");
+    }
+    if ((pa.type != cudaMemoryTypeDevice && pa.type != cudaMemoryTypeManaged) || pa.device != cur)
+        return fail(QS_EINVAL, "qs_probs_noalloc: dev_amp must be device memory of the current device");
+    // The call synchronises and copies into pageable host memory, neither of which a stream
+    // capture allows.
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing((cudaStream_t)stream, &cap) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(QS_EINVAL, "qs_probs_noalloc: invalid stream");
+    }
+    if (cap != cudaStreamCaptureStatusNone)
+        return fail(QS_EINVAL, "qs_probs_noalloc: the stream is being captured");
     LaunchCtx c{const_cast<void *>(dev_amp), n, dt, stream};
     char err[256] = {0};
     const int rc = launch_probs_static(c, phys, nq, host_out, err, sizeof err);

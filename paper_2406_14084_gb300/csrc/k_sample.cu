@@ -179,11 +179,12 @@ __global__ void sample_kernel(const typename Cx<R>::T *__restrict__ a, int blog,
     if (k >= shots) return;
     const double total = P[M];
     const double t = u[k] * total;
-    // last block j with P[j] <= t (P is non-decreasing, P[0] = 0)
+    // last block j with P[j] <= t (P is non-decreasing, P[0] = 0); P[j] < total keeps the
+    // search off trailing zero-weight blocks even if t reached the total
     uint64_t lo = 0, hi = M - 1;
     while (lo < hi) {
         const uint64_t mid = lo + (hi - lo + 1) / 2;
-        if (P[mid] <= t) lo = mid;
+        if (P[mid] <= t && P[mid] < total) lo = mid;
         else hi = mid - 1;
     }
     const uint64_t j = lo, base = j << blog, len = uint64_t(1) << blog;

@@ -288,6 +288,20 @@ qs_status qs_model_get_params(const qs_model *m, float *host, size_t count)
     return cuda_fail(cudaMemcpy(host, m->params, count * sizeof(float), cudaMemcpyDeviceToHost), "parameter download");
 }
 
+qs_status qs_model_get_moments(const qs_model *m, float *mom, float *vel, size_t count)
+{
+    if (!m || !mom || !vel) return set_error(QS_EINVAL, "NULL argument");
+    if (count != (size_t)m->P) return set_error(QS_EINVAL, "count must equal the parameter count");
+    qs_model *mm = const_cast<qs_model *>(m);
+    std::lock_guard<std::mutex> g(mm->lock);
+    cudaStreamSynchronize(mm->stream);
+    qs_status st = cuda_fail(cudaMemcpy(mom, m->adam_m, count * sizeof(float), cudaMemcpyDeviceToHost),
+                             "first-moment download");
+    if (st) return st;
+    return cuda_fail(cudaMemcpy(vel, m->adam_v, count * sizeof(float), cudaMemcpyDeviceToHost),
+                     "second-moment download");
+}
+
 qs_status qs_model_set_params(qs_model *m, const float *host, size_t count)
 {
     if (!m || !host) return set_error(QS_EINVAL, "NULL argument");

@@ -148,6 +148,7 @@ _SIGS = {
     "qs_model_info_get": [_vp, ctypes.POINTER(QsModelInfo)],
     "qs_model_get_params": [_vp, _fp, ctypes.c_size_t],
     "qs_model_set_params": [_vp, _fp, ctypes.c_size_t],
+    "qs_model_get_moments": [_vp, _fp, _fp, ctypes.c_size_t],
     "qs_model_get_norm": [_vp, _fp, _fp, _fp, _fp],
     "qs_model_set_norm": [_vp, _fp, _fp, ctypes.c_float, ctypes.c_float],
     "qs_model_predict": [_vp, _fp, ctypes.c_size_t, _fp],
@@ -376,6 +377,14 @@ def qs_model_get_params(model) -> np.ndarray:
     out = np.zeros(qs_model_info_get(model)["nparams"], dtype=np.float32)
     _check(lib().qs_model_get_params(model, _f32(out), out.size))
     return out
+
+
+def qs_model_get_moments(model):
+    """Adam's first and second moment estimates (m, v), one entry per parameter."""
+    k = qs_model_info_get(model)["nparams"]
+    m, v = np.zeros(k, dtype=np.float32), np.zeros(k, dtype=np.float32)
+    _check(lib().qs_model_get_moments(model, _f32(m), _f32(v), k))
+    return m, v
 
 
 def qs_model_set_params(model, params):

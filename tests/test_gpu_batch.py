@@ -43,6 +43,27 @@ def test_batch_matches_oracle(dtype, graph):
         qs.qs_batch_destroy(b)
 
 
+@pytest.mark.parametrize("dtype", [qs.QS_C64, qs.QS_C128])
+def test_batch_full_range_circuits_match_oracle(dtype):
+    """The batch configuration's extremes: circuits of up to 24 qubits and 12 layers (slabs run
+    multi-pass with the most items per pass) mixed with small ones, on the graph path."""
+    shapes = [(24, 12, 71), (24, 7, 72), (22, 12, 73), (20, 2, 74), (17, 12, 75), (13, 9, 76),
+              (11, 12, 77), (10, 2, 78)]
+    circuits = [(n, W.vqe_circuit(n, L, seed)) for n, L, seed in shapes]
+    want = oracle_expect(circuits)
+    b = qs.qs_batch_create(circuits, qs.options(dtype=dtype, graph=1))
+    try:
+        info = qs.qs_batch_info_get(b)
+        assert info["rounds"] >= 2
+        for _ in range(2):
+            got = qs.qs_apply_batch(b, H_TERMS, len(circuits))
+            ns = np.array([c[0] for c in circuits])
+            tol = (1e-9 if dtype == qs.QS_C128 else 1e-4) * ns
+            assert np.all(np.abs(got - want) <= tol), np.max(np.abs(got - want))
+    finally:
+        qs.qs_batch_destroy(b)
+
+
 def test_batch_small_slab_forces_multipass_and_tuner():
     circuits = W.vqe_batch(12, 99, nmin=12, nmax=16, lmin=2, lmax=3)
     want = oracle_expect(circuits)

@@ -5,8 +5,9 @@ size:
 - the no-swap QFT of a basis state |x> (32 qubits, complex128, 64 GiB) has the closed form
   a(y) = 2^{-n/2} exp(2 pi i x rev(y) / 2^n), compared on sampled runs of amplitudes
   (the same closed form pins the oracle);
-- a layered circuit followed by its inverse (34 qubits, complex64, 128 GiB) returns the basis
-  state it started from, and every pass preserves the norm.
+- a layered circuit followed by its inverse (32 qubits complex128, 64 GiB; 34 qubits complex64,
+  128 GiB) returns the basis state it started from, the norm is preserved, and the marginal
+  probabilities of sampled qubits are those of the basis state.
 """
 import math
 
@@ -89,5 +90,40 @@ def test_layered34_complex64_inverse_returns_basis_state():
         want = np.zeros(8)
         want[(x0 & 1) | ((x0 >> 33) & 1) << 1 | ((x0 >> 17) & 1) << 2] = 1.0
         assert np.max(np.abs(p - want)) <= 2e-4
+    finally:
+        s.close()
+
+
+def test_layered32_complex128_inverse_returns_basis_state():
+    """The 32-qubit complex128 layered circuit of depth 40 with the bench's default options, then
+    its inverse: back to the start state within 1e-10 (the complex128 amplitude bar is 1e-12
+    per amplitude for one circuit; U then U^-1 doubles the rounding)."""
+    n = 32
+    if free_gib() < 70:
+        pytest.skip("needs 64 GiB of free device memory")
+    g = W.layered(n, 40, 1002)
+    x0 = 0x9C3A5A17 & ((1 << n) - 1)
+    s = qs.State(n, qs.QS_C128)
+    try:
+        s.set_basis(x0)
+        s.apply(g, qs.options(dtype=qs.QS_C128))
+        assert abs(s.norm2() - 1.0) <= 1e-12
+        mid = s.probs([0, 31, 16, 7])
+        assert abs(mid.sum() - 1.0) <= 1e-12 and np.all(mid >= 0)
+        s.apply(inverse_layered(g), qs.options(dtype=qs.QS_C128))
+        assert abs(s.norm2() - 1.0) <= 1e-12
+        a = qs.qs_copy_to_host(s.h, n, qs.QS_C128, x0, 1)[0]
+        assert abs(a - 1.0) <= 1e-10, a
+        rng = np.random.default_rng(3)
+        for _ in range(3):
+            qubits = [int(q) for q in rng.choice(n, size=5, replace=False)]
+            p = s.probs(qubits)
+            want = np.zeros(32)
+            want[sum(((x0 >> q) & 1) << j for j, q in enumerate(qubits))] = 1.0
+            assert np.max(np.abs(p - want)) <= 1e-10
+        # amplitudes around the start state are zero
+        near = qs.qs_copy_to_host(s.h, n, qs.QS_C128, (x0 & ~511), 512)
+        near[x0 & 511] = 0.0
+        assert np.max(np.abs(near)) <= 1e-10
     finally:
         s.close()

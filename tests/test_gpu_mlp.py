@@ -1,8 +1,8 @@
 """Cost-model network kernels against the FP64 oracle MLP.
 
 Forward to 1e-5 (relative to the output scale), gradients to 1e-4 relative (norm-wise and for
-every entry above 1% of the largest), one Adam step against the oracle's Adam step, and a
-training run that fits a known function."""
+every entry above 1% of the largest), one and three Adam steps (parameters and moments) against
+the oracle's Adam steps, and a training run that fits a known function."""
 import numpy as np
 import pytest
 
@@ -87,6 +87,43 @@ def test_one_adam_step_matches_oracle():
         assert np.max(np.abs((got - p) - (want - p))[sure]) <= 2e-4 * lr + 1e-6
         assert np.max(np.abs(got - p)) <= lr * (1 + 1e-3)
         assert qs.qs_model_info_get(m)["steps"] == 1
+    finally:
+        qs.qs_model_destroy(m)
+
+
+def test_three_adam_steps_match_oracle():
+    """Three full-batch Adam steps (Kingma & Ba, Algorithm 1): parameters and both moment
+    estimates against the oracle's FP64 steps, each taken at the oracle's own gradient of the
+    current parameters.  From the second step on the update depends on beta1, beta2 and both
+    bias corrections, which the first step does not."""
+    F, B, lr = 9, 64, 1e-2
+    m, p = random_model(F, 17)
+    try:
+        rng = np.random.default_rng(19)
+        X = rng.normal(0, 1, (B, F)).astype(np.float32)
+        T = rng.normal(0, 1, B).astype(np.float32)
+        want = p.astype(np.float64).copy()
+        mom, vel = np.zeros_like(want), np.zeros_like(want)
+        grads = []
+        for t in (1, 2, 3):
+            _, g = oracle.mlp_loss_grad(X.astype(np.float64), T.astype(np.float64), split(want, F))
+            g = np.concatenate([a.ravel() for a in g])
+            grads.append(g)
+            oracle.adam_step(want, g, mom, vel, t, lr=lr, beta1=0.9, beta2=0.999, eps=1e-8)
+        qs.qs_model_train(m, X, T, qs.qs_train_options(epochs=3, batch=B, lr=lr, fit_norm=0, graph=0))
+        assert qs.qs_model_info_get(m)["steps"] == 3
+        got = qs.qs_model_get_params(m).astype(np.float64)
+        gm, gv = (a.astype(np.float64) for a in qs.qs_model_get_moments(m))
+        gmax = max(float(np.max(np.abs(g))) for g in grads)
+        # moments are sums of FP32 gradients: compare against the gradient scale
+        assert np.max(np.abs(gm - mom)) <= 1e-4 * gmax
+        assert np.max(np.abs(gv - vel)) <= 1e-4 * gmax * gmax + 1e-3 * np.max(np.abs(vel))
+        # parameter moves where every step's gradient is clearly above the FP32 sum noise
+        sure = np.all([np.abs(g) > 1e-3 * gmax for g in grads], axis=0)
+        assert sure.sum() > 0.5 * sure.size
+        assert np.max(np.abs((got - p) - (want - p))[sure]) <= 1e-3 * lr
+        # Adam moves each parameter by at most about lr per step
+        assert np.max(np.abs(got - p)) <= 3 * lr * (1 + 1e-3)
     finally:
         qs.qs_model_destroy(m)
 

@@ -75,3 +75,18 @@ def test_sample_rejects_zero_state():
         qs.qs_copy_from_host(s.h, np.zeros(1 << n, dtype=np.complex64))
         with pytest.raises(qs.QsError):
             s.sample([0.5])
+
+
+@pytest.mark.parametrize("dtype", [qs.QS_C64, qs.QS_C128])
+@pytest.mark.parametrize("n", [9, 13, 18])
+def test_sample_top_uniform_skips_trailing_zero_weight(dtype, n):
+    """u just below 1 on a state whose upper half has zero weight (Born rule, Eq. 1: an outcome
+    of zero probability is never drawn): the draw is the last outcome of positive weight."""
+    u = np.array([np.nextafter(1.0, 0.0), 1.0 - 1e-12, 0.25 + 0.5 / (1 << (n - 1))])  # last: mid-step
+    with qs.State(n, dtype) as s:
+        s.apply([Gate("H", (q,)) for q in range(n - 1)], qs.options(dtype=dtype))
+        got = s.sample(u)
+        amps = s.amplitudes().astype(np.complex128)
+    top = (1 << (n - 1)) - 1
+    assert got[0] == top and got[1] == top
+    assert np.array_equal(got, oracle.sample(amps, n, u))

@@ -68,3 +68,16 @@ def test_mixed_circuit_tc_and_simt_steps():
     assert st["tc_gates"] > 0
     assert infidelity(want, got) <= 1e-6
     assert np.max(np.abs(got - want)) <= 1e-5
+
+
+def test_layered_24_qubits_on_tensor_cores():
+    """A 24-qubit state (128 MiB complex64, larger than L2): many slabs per tensor-core launch,
+    targets spread over all 24 qubits."""
+    n = 24
+    gates = W.layered(n, 6, 1003)
+    init = oracle.basis_state(n, 0x5A5A5A)
+    want = oracle.apply_circuit(n, gates, init.copy())
+    got, st = run_tc(n, gates, init)
+    assert st["tc_gates"] >= 4
+    assert infidelity(want, got) <= 1e-6
+    assert np.max(np.abs(got - want)) <= 1e-5

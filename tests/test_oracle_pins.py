@@ -473,6 +473,37 @@ def test_adam_first_step_moves_by_lr_times_sign():
     assert np.allclose(p, [1.0 - 0.01, -2.0 + 0.01, 3.0 - 0.01], atol=1e-9)
 
 
+def test_adam_steps_two_and_three_by_hand():
+    """Kingma & Ba, Algorithm 1, worked by hand with beta1 = 1/2, beta2 = 3/4, eps = 0 and
+    lr = 1/10 on one parameter p0 = 1 with gradients 2, 1, -4 (moments start at zero):
+      t = 1: m = 1,    v = 1,    m_hat = 1 / (1/2) = 2,        v_hat = 1 / (1/4) = 4,
+             p1 = 1 - 0.1 * 2 / 2 = 0.9
+      t = 2: m = 1,    v = 1,    m_hat = 1 / (3/4) = 4/3,      v_hat = 1 / (7/16) = 16/7,
+             p2 = p1 - 0.1 * (4/3) / (4 / sqrt 7) = 0.9 - 0.1 * sqrt(7) / 3
+      t = 3: m = -3/2, v = 19/4, m_hat = -(3/2) / (7/8) = -12/7, v_hat = (19/4) / (37/64) = 304/37,
+             p3 = p2 + 0.1 * (12/7) / sqrt(304/37)
+    A swapped beta, a moment update with the wrong weight or a bias correction with the wrong
+    power changes p2 or p3.  A second parameter starts from non-zero moments at t = 2:
+      m = 0.3, v = 0.5, g = 0.1:  m' = 0.2, v' = 0.3775,
+      p' = 0 - 0.1 * (0.2 / (3/4)) / sqrt(0.3775 / (7/16))."""
+    p = np.array([1.0])
+    m, v = np.zeros(1), np.zeros(1)
+    kw = dict(lr=0.1, beta1=0.5, beta2=0.75, eps=0.0)
+    oracle.adam_step(p, np.array([2.0]), m, v, 1, **kw)
+    assert p[0] == pytest.approx(0.9, abs=1e-15) and m[0] == 1.0 and v[0] == 1.0
+    oracle.adam_step(p, np.array([1.0]), m, v, 2, **kw)
+    p2 = 0.9 - 0.1 * math.sqrt(7.0) / 3.0
+    assert (m[0], v[0]) == (1.0, 1.0)
+    assert p[0] == pytest.approx(p2, abs=1e-15)
+    oracle.adam_step(p, np.array([-4.0]), m, v, 3, **kw)
+    assert m[0] == pytest.approx(-1.5, abs=1e-15) and v[0] == pytest.approx(4.75, abs=1e-15)
+    assert p[0] == pytest.approx(p2 + 0.1 * (12.0 / 7.0) / math.sqrt(304.0 / 37.0), abs=1e-14)
+    q, qm, qv = np.array([0.0]), np.array([0.3]), np.array([0.5])
+    oracle.adam_step(q, np.array([0.1]), qm, qv, 2, **kw)
+    assert qm[0] == pytest.approx(0.2, abs=1e-15) and qv[0] == pytest.approx(0.3775, abs=1e-15)
+    assert q[0] == pytest.approx(-0.1 * (0.2 / 0.75) / math.sqrt(0.3775 / 0.4375), abs=1e-14)
+
+
 def test_sampling_inverse_transform_pins():
     """Born-rule sampling by inverse transform: closed forms that fix the index order, the
     strict inequality at CDF steps, and the normalisation by the total weight."""
