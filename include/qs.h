@@ -107,7 +107,11 @@ typedef struct {
     int32_t euler;       /* blocked plans: write complex 1-qubit gates as phase, real rotation,
                             phase (Z-Y-Z) so that register stages merge the phases.  0 or 2 =
                             split (the default), 1 = keep complex 2x2 matrices */
-    int32_t reserved[2];
+    int32_t factor;      /* register stages: write each real 2x2 gate M as D N, N with two unit
+                            entries (one FMA per real output instead of two) and D diagonal
+                            (folded into the stage's diagonal tables).  0 = on (the default),
+                            1 = off */
+    int32_t reserved[1];
 } qs_options;
 
 /* Plan summary (qs_plan_info). */

@@ -775,9 +775,29 @@ qs_status qs_plan_dump(const qs_plan *pl, char *buf, size_t cap, size_t *needed)
                         for (size_t e = 0; e < (sb.type == SB_G2 ? 16u : 4u); ++e) cnum(p.coef[sb.mat + e]);
                         break;
                     }
+                    case SB_G1N:
+                    case SB_G1A: {
+                        head("DENSE", {reg_phys(sb.j0)}, ctl);
+                        out += " m";
+                        const cd x = p.coef[sb.mat], y = p.coef[sb.mat + 1], one(1.0);
+                        if (sb.type == SB_G1N) {
+                            cnum(one); cnum(x); cnum(y); cnum(one);
+                        } else {
+                            cnum(x); cnum(one); cnum(one); cnum(y);
+                        }
+                        break;
+                    }
                     case SB_X: head("PERMX", {reg_phys(sb.j0)}, ctl); break;
                     case SB_SWAP: head("SWAP", {reg_phys(sb.j0), reg_phys(sb.j1)}, ctl); break;
                     case SB_PHASE: {
+                        if (ctl.empty()) {
+                            // a scalar on every element: a diagonal of equal entries on one qubit
+                            head("DIAG", {reg_phys(0)}, {});
+                            out += " m";
+                            cnum(p.coef[sb.mat]);
+                            cnum(p.coef[sb.mat]);
+                            break;
+                        }
                         // controlled phase: diagonal over every masked qubit, 1 except all-ones
                         head("DIAG", ctl, {});
                         out += " m";

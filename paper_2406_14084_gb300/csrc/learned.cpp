@@ -71,6 +71,12 @@ void tally_sub(const DevSub &sb, float *f)
         f[27] = std::max(f[27], 1.f);
         if (ctl) f[25] += 1;
         break;
+    case SB_G1N:
+    case SB_G1A:
+        f[17] += 1;
+        f[26] += float(2.0 * act);
+        f[27] = std::max(f[27], 1.f);
+        break;
     case SB_G2:
         f[18] += 1;
         f[26] += float(16.0 * act);

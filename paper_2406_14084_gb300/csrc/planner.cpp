@@ -613,7 +613,7 @@ void merge_stage_diagonals(Plan &plan, int s0, int RB, Coefs &cf)
     const int ns = (int)in.size();
     auto target_bits = [](const DevSub &s) -> uint32_t {
         switch (s.type) {
-        case SB_G1: case SB_G1R: case SB_X: return 1u << s.j0;
+        case SB_G1: case SB_G1R: case SB_G1N: case SB_G1A: case SB_X: return 1u << s.j0;
         case SB_G2: case SB_SWAP: return (1u << s.j0) | (1u << s.j1);
         default: return 0;
         }
@@ -739,6 +739,77 @@ void merge_stage_diagonals(Plan &plan, int s0, int RB, Coefs &cf)
         if (!merged[i]) out.push_back(in[i]);
     }
     for (const DevSub &s : at[m]) out.push_back(s);
+    plan.subs.resize(s0);
+    plan.subs.insert(plan.subs.end(), out.begin(), out.end());
+}
+
+// Write each uncontrolled real 2x2 sub M of a stage (rotations, H) as M = D N, where N has two
+// unit entries -- N = [[1, m01/m00], [m10/m11, 1]] with D = diag(m00, m11) when |m00| >= |m01|,
+// else N = [[m00/m01, 1], [1, m11/m10]] with D = diag(m01, m10) -- so that N costs one FMA per
+// real output instead of two, and every ratio is at most 1 in magnitude.  For an orthogonal M,
+// |d1| = |d0|: D = d0 diag(1, d1/d0) with d1/d0 = +-1.  The sign becomes a phase sub on the target
+// bit right after N, and the real scalars d0 of all factored subs are collected into one scalar
+// sub of the stage (a diagonal that reads no bit); the diagonal merge that follows folds both
+// into the stage's tables where that pays.  The matrices stay FP64 products of the gate's own
+// entries (Eq. 2-3 reassociated), so results change only by rounding.
+void factor_stage_rotations(Plan &plan, int s0, Coefs &cf)
+{
+    if (plan.opt.factor == 1) return;
+    std::vector<DevSub> in(plan.subs.begin() + s0, plan.subs.end());
+    int cand = 0;
+    bool has_diag = false;
+    for (const DevSub &sb : in) {
+        if (sb.type == SB_G1R && !(sb.scm | sb.lcm | sb.ocm)) ++cand;
+        if (sb.type == SB_PHASE || sb.type == SB_DIAG) has_diag = true;
+    }
+    // the stage scalar costs one multiply per amplitude unless a table absorbs it
+    if (cand == 0 || (cand < 2 && !has_diag)) return;
+    double sigma = 1.0;
+    std::vector<DevSub> out;
+    out.reserve(in.size() + cand + 1);
+    for (const DevSub &sb : in) {
+        if (sb.type != SB_G1R || (sb.scm | sb.lcm | sb.ocm)) {
+            out.push_back(sb);
+            continue;
+        }
+        const double m00 = plan.coef[sb.mat].real(), m01 = plan.coef[sb.mat + 1].real();
+        const double m10 = plan.coef[sb.mat + 2].real(), m11 = plan.coef[sb.mat + 3].real();
+        DevSub f = sb;
+        double x, y, d0, d1;
+        if (std::abs(m00) >= std::abs(m01)) {
+            f.type = SB_G1N;
+            d0 = m00;
+            d1 = m11;
+            x = m01 / m00;
+            y = d1 != 0.0 ? m10 / m11 : 0.0;
+        } else {
+            f.type = SB_G1A;
+            d0 = m01;
+            d1 = m10;
+            x = m00 / m01;
+            y = d1 != 0.0 ? m11 / m10 : 0.0;
+        }
+        if (d0 == 0.0 || std::abs(std::abs(d1) - std::abs(d0)) > 1e-12 * std::abs(d0)) {
+            out.push_back(sb);  // not orthogonal: keep the full matrix
+            continue;
+        }
+        f.mat = cf.push(std::vector<cd>{cd(x), cd(y)});
+        out.push_back(f);
+        sigma *= d0;
+        if ((d1 < 0) != (d0 < 0)) {
+            DevSub sg;
+            std::memset(&sg, 0, sizeof sg);
+            sg.type = SB_PHASE;
+            sg.scm = 1u << sb.j0;
+            sg.mat = cf.push(std::vector<cd>{cd(-1.0)});
+            out.push_back(sg);
+        }
+    }
+    DevSub sc;
+    std::memset(&sc, 0, sizeof sc);
+    sc.type = SB_PHASE;
+    sc.mat = cf.push(std::vector<cd>{cd(sigma)});
+    out.push_back(sc);
     plan.subs.resize(s0);
     plan.subs.insert(plan.subs.end(), out.begin(), out.end());
 }
@@ -930,6 +1001,7 @@ void build_stages(Plan &plan, const std::vector<CGate> &gates, const std::vector
             }
             plan.subs.push_back(s);
         }
+        factor_stage_rotations(plan, st.sub_begin, cf);
         merge_stage_diagonals(plan, st.sub_begin, RB, cf);
         st.sub_end = (int)plan.subs.size();
         DevOp op;

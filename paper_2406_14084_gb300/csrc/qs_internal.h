@@ -76,6 +76,8 @@ enum SubType : uint8_t {
     SB_PHASE = 4,  // multiply by coef[mat] where all masked bits are 1 (controlled phase)
     SB_DIAG = 5,   // diagonal table expanded over all register bits (see DevSub)
     SB_G1R = 6,    // 2x2 matrix with real entries on register bit j0
+    SB_G1N = 7,    // real [[1, x], [y, 1]] on register bit j0 (coef[mat] = x, coef[mat + 1] = y)
+    SB_G1A = 8,    // real [[x, 1], [1, y]] on register bit j0 (coef[mat] = x, coef[mat + 1] = y)
 };
 
 // 48 bytes, 16-byte aligned: the kernels fetch the first 24 bytes with one 16-byte and one

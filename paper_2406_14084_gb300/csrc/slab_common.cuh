@@ -89,8 +89,9 @@ __device__ __forceinline__ void sub_g2(C (&v)[1 << RB], const C *__restrict__ M,
 }
 
 // Phase p on the elements whose bits MASK are all set (MASK is a compile-time constant).
+// neg: p = -1 (sign flip); real: p has no imaginary part (two multiplies per element).
 template <typename C, int RB, int MASK, int UNUSED>
-__device__ __forceinline__ void sub_phase_mask(C (&v)[1 << RB], C p, bool neg)
+__device__ __forceinline__ void sub_phase_mask(C (&v)[1 << RB], C p, bool neg, bool real = false)
 {
     if (neg) {
 #pragma unroll
@@ -98,6 +99,13 @@ __device__ __forceinline__ void sub_phase_mask(C (&v)[1 << RB], C p, bool neg)
             if ((e & MASK) == MASK) {
                 v[e].x = -v[e].x;
                 v[e].y = -v[e].y;
+            }
+    } else if (real) {
+#pragma unroll
+        for (int e = 0; e < (1 << RB); ++e)
+            if ((e & MASK) == MASK) {
+                v[e].x *= p.x;
+                v[e].y *= p.x;
             }
     } else {
 #pragma unroll
@@ -129,6 +137,45 @@ __device__ __forceinline__ void sub_g1r(C (&v)[1 << RB], const C *__restrict__ M
 {
     if (scm == 0) sub_g1r_impl<C, RB, J, false>(v, M, 0);
     else sub_g1r_impl<C, RB, J, true>(v, M, scm);
+}
+
+// Real 2x2 with two unit entries, uncontrolled: one FMA per real output.
+//   ANTI = false: [[1, x], [y, 1]]: a' = a + x b, b' = y a + b
+//   ANTI = true:  [[x, 1], [1, y]]: a' = x a + b, b' = a + y b
+template <typename C, int RB, int J, bool ANTI>
+__device__ __forceinline__ void sub_g1n(C (&v)[1 << RB], const C *__restrict__ M)
+{
+    const auto x = M[0].x, y = M[1].x;
+#pragma unroll
+    for (int e = 0; e < (1 << RB); ++e) {
+        if (e & (1 << J)) continue;
+        const int e1 = e | (1 << J);
+        const C a = v[e], b = v[e1];
+        if (ANTI) {
+            v[e].x = fma(x, a.x, b.x);
+            v[e].y = fma(x, a.y, b.y);
+            v[e1].x = fma(y, b.x, a.x);
+            v[e1].y = fma(y, b.y, a.y);
+        } else {
+            v[e].x = fma(x, b.x, a.x);
+            v[e].y = fma(x, b.y, a.y);
+            v[e1].x = fma(y, a.x, b.x);
+            v[e1].y = fma(y, a.y, b.y);
+        }
+    }
+}
+
+template <typename C, int RB, bool ANTI>
+__device__ __forceinline__ void sub_g1n_j(C (&v)[1 << RB], const C *__restrict__ M, uint32_t j0)
+{
+    switch (j0) {
+    case 0: sub_g1n<C, RB, 0, ANTI>(v, M); break;
+    case 1: sub_g1n<C, RB, 1, ANTI>(v, M); break;
+    case 2: sub_g1n<C, RB, 2, ANTI>(v, M); break;
+    case 3: sub_g1n<C, RB, 3, ANTI>(v, M); break;
+    case 4: if (RB > 4) sub_g1n<C, RB, (RB > 4 ? 4 : 0), ANTI>(v, M); break;
+    default: break;
+    }
 }
 
 template <typename C, int RB, int J>
@@ -244,7 +291,7 @@ __device__ __forceinline__ void apply_sub(C (&v)[1 << RB], const SubHead &h, con
         const bool neg = (p.x == -1 && p.y == 0);
         const int pc = __popc(scm);
         if (pc == 0) {
-            sub_phase_mask<C, RB, 0, 0>(v, p, neg);
+            sub_phase_mask<C, RB, 0, 0>(v, p, neg, p.y == 0);  // a scalar; real for factored stages
         } else if (pc == 1) {
             switch (__ffs(scm) - 1) {
             case 0: sub_phase_mask<C, RB, 1, 0>(v, p, neg); break;
@@ -285,6 +332,8 @@ __device__ __forceinline__ void apply_sub(C (&v)[1 << RB], const SubHead &h, con
         default: break;
         }
         break;
+    case SB_G1N: sub_g1n_j<C, RB, false>(v, M, j0); break;
+    case SB_G1A: sub_g1n_j<C, RB, true>(v, M, j0); break;
     case SB_DIAG: {
         uint32_t hi = 0;
         for (int j = 0; j < int(ndl); ++j) {

@@ -54,7 +54,8 @@ class QsOptions(ctypes.Structure):
                 ("tc_width", ctypes.c_int32), ("graph", ctypes.c_int32),
                 ("diag_bits", ctypes.c_int32), ("dtype", ctypes.c_int32),
                 ("stage_bits", ctypes.c_int32), ("fuse_force", ctypes.c_int32),
-                ("euler", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
+                ("euler", ctypes.c_int32), ("factor", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 1)]
 
 
 class QsPlanInfo(ctypes.Structure):

@@ -118,10 +118,13 @@ def test_three_adam_steps_match_oracle():
         # moments are sums of FP32 gradients: compare against the gradient scale
         assert np.max(np.abs(gm - mom)) <= 1e-4 * gmax
         assert np.max(np.abs(gv - vel)) <= 1e-4 * gmax * gmax + 1e-3 * np.max(np.abs(vel))
-        # parameter moves where every step's gradient is clearly above the FP32 sum noise
+        # parameter moves where every step's gradient is clearly above the FP32 sum noise (units
+        # whose ReLU is off for every row have exactly zero gradients and do not move)
         sure = np.all([np.abs(g) > 1e-3 * gmax for g in grads], axis=0)
-        assert sure.sum() > 0.5 * sure.size
+        zero = np.all([g == 0 for g in grads], axis=0)
+        assert sure.sum() > 0.25 * sure.size
         assert np.max(np.abs((got - p) - (want - p))[sure]) <= 1e-3 * lr
+        assert np.max(np.abs(got - p)[zero], initial=0.0) <= 1e-3 * lr
         # Adam moves each parameter by at most about lr per step
         assert np.max(np.abs(got - p)) <= 3 * lr * (1 + 1e-3)
     finally:

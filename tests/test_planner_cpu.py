@@ -13,6 +13,7 @@ from paper_2406_14084_gb300 import qs
 from paper_2406_14084_gb300 import workloads as W
 from paper_2406_14084_gb300.workloads import Gate
 
+import plan_replay as PR
 from plan_replay import replay, to_logical
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -153,10 +154,10 @@ def test_diagonal_gates_need_no_slab_residence():
 def test_uncontrolled_swaps_are_relabels():
     n = 8
     gates = [Gate("H", (0,)), Gate("SWAP", (0, 7)), Gate("RY", (7,), (), (0.3,)), Gate("SWAP", (3, 5))]
-    info, stats = check_plan(gates, n, qs.options(slab_bits=5, seg_bits=2))
+    info, stats = check_plan(gates, n, qs.options(slab_bits=5, seg_bits=2, factor=1))
     # the relabel renames RY's qubit onto H's, so both fuse into one 1-qubit op
     assert stats["ops"] == 1
-    info, stats = check_plan(gates, n, qs.options(slab_bits=5, seg_bits=2, fuse_width=0))
+    info, stats = check_plan(gates, n, qs.options(slab_bits=5, seg_bits=2, fuse_width=0, factor=1))
     assert stats["ops"] == 2
 
 
@@ -287,3 +288,27 @@ def test_euler_split_is_the_default_and_can_be_turned_off():
             qs.qs_plan_destroy(p)
     for dtype in (qs.QS_C64, qs.QS_C128):
         assert counts[dtype, 0] == counts[dtype, 2] > 0 and counts[dtype, 1] == 0
+
+
+@pytest.mark.parametrize("dtype", [qs.QS_C64, qs.QS_C128])
+def test_factored_rotations_replay_against_oracle(dtype):
+    """Register-stage real 2 x 2 gates written as D N (N with two unit entries, D folded into the
+    stage tables): the listing holds such N matrices, and replaying it on the oracle gives the
+    circuit's state.  Rotations with |cos| < |sin| take the anti-diagonal form."""
+    n = 11
+    gates = W.layered(n, 6, 31) + [Gate("H", (q,)) for q in range(n)]
+    gates += [Gate("RY", (q,), (), (2.6 + 0.05 * q,)) for q in range(n)]  # |cos| < |sin|
+    gates += W.qft(n)
+    plan = qs.qs_fuse(gates, n, qs.options(dtype=dtype))
+    text = qs.qs_plan_dump(plan)
+    qs.qs_plan_destroy(plan)
+    _, items, _ = PR.parse_dump(text)
+    unit = anti = 0
+    for it in items:
+        if it[0] == "OP" and it[1] == "DENSE" and len(it[2]) == 1 and not it[3]:
+            m = it[4]
+            unit += int(m[0, 0] == 1 and m[1, 1] == 1)
+            anti += int(m[0, 1] == 1 and m[1, 0] == 1)
+    assert unit > 0 and anti > 0
+    check_plan(gates, n, qs.options(dtype=dtype))
+    off, _ = check_plan(gates, n, qs.options(dtype=dtype, factor=1))
