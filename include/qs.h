@@ -81,6 +81,9 @@ typedef struct {
 } qs_pauli_term;
 
 typedef enum { QS_PLANNER_GREEDY = 0, QS_PLANNER_LEARNED = 1 } qs_planner;
+/* Tensor-core modes for fused 6-qubit gates on complex64 states: split precision with three
+ * products (hi*hi + hi*lo + lo*hi) and FP32 accumulation, parts in TF32 (about 22 significant
+ * bits for hi + lo) or BF16 (about 16 bits).  Not in the paper: a GB300 form of its dense gates. */
 typedef enum { QS_TC_OFF = 0, QS_TC_TF32X3 = 1, QS_TC_BF16X3 = 2 } qs_tc_mode;
 typedef enum { QS_SLAB_GATHER = 0, QS_SLAB_REMAP = 1 } qs_slab_mode;
 
@@ -111,7 +114,9 @@ typedef struct {
                             entries (one FMA per real output instead of two) and D diagonal
                             (folded into the stage's diagonal tables).  0 = on (the default),
                             1 = off */
-    int32_t reserved[1];
+    int32_t merge_bits;  /* register stages: most condition bits (slab or outer qubits) one merged
+                            diagonal table may read besides the register bits; 0 = automatic (6),
+                            at most 10 (tables of 2^(stage_bits + merge_bits) entries) */
 } qs_options;
 
 /* Plan summary (qs_plan_info). */
@@ -289,7 +294,8 @@ qs_status qs_expect_pauli_sum(qs_state *s, const qs_pauli_term *terms, size_t nt
  * work items from a queue in dependency order, waiting (bounded) for a circuit's previous pass
  * to be stored before starting its next one.  A circuit whose state fits one slab (n <= slab
  * bits) runs entirely in shared memory.  The first pass prepares |0..0> in place; the last one
- * also accumulates the circuit's expectation value.  qs_apply_batch replays the launch from a
+ * accumulates the circuit's expectation value from a Walsh-Hadamard transform of each slab's
+ * probabilities and stores nothing (the final states are not kept).  qs_apply_batch replays the launch from a
  * captured CUDA graph when options.graph is set.  Not in the paper (a library service). */
 typedef struct qs_batch qs_batch;
 

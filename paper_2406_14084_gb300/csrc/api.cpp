@@ -195,7 +195,8 @@ qs_status upload(qs_plan *pl, qs_dtype dt)
     const size_t ntc = std::max<size_t>(1, p.tcs.size()), nim = std::max<size_t>(16, p.tc_images.size());
     const size_t o_tc = o_sb + al(nsb * sizeof(DevSub)), o_im = o_tc + al(ntc * sizeof(DevTc));
     const size_t o_coef = o_im + al(nim);
-    const size_t total = o_coef + al(nc * amp_bytes(dt));
+    // two spare entries: the register stages read a sub-op's first two coefficients ahead
+    const size_t total = o_coef + al((nc + 2) * amp_bytes(dt));
     std::vector<unsigned char> h(total, 0);
     if (!p.passes.empty()) std::memcpy(h.data() + o_pass, p.passes.data(), p.passes.size() * sizeof(DevPass));
     if (!p.ops.empty()) std::memcpy(h.data() + o_ops, p.ops.data(), p.ops.size() * sizeof(DevOp));
@@ -559,7 +560,8 @@ qs_status qs_fuse(const qs_gate *g, size_t ng, int n, const qs_options *o, qs_pl
     if (o) opt = *o;
     else qs_options_default(&opt);
     if (opt.fuse_width < 0 || opt.fuse_width > 7 || opt.slab_bits < 0 || opt.slab_bits > kMaxSlabBits ||
-        opt.seg_bits < 0 || opt.seg_bits > 8 || (opt.slab_mode != QS_SLAB_GATHER && opt.slab_mode != QS_SLAB_REMAP) ||
+        opt.seg_bits < 0 || opt.seg_bits > 8 || opt.merge_bits < 0 || opt.merge_bits > 10 ||
+        (opt.slab_mode != QS_SLAB_GATHER && opt.slab_mode != QS_SLAB_REMAP) ||
         (opt.tc != QS_TC_OFF && opt.tc != QS_TC_TF32X3 && opt.tc != QS_TC_BF16X3))
         return fail(QS_EINVAL, "option out of range");
     std::vector<CGate> cg;
@@ -589,7 +591,8 @@ qs_status qs_fuse_learned(const qs_gate *g, size_t ng, int n, const qs_options *
     if (o) opt = *o;
     else qs_options_default(&opt);
     if (opt.fuse_width < 0 || opt.fuse_width > 7 || opt.slab_bits < 0 || opt.slab_bits > kMaxSlabBits ||
-        opt.seg_bits < 0 || opt.seg_bits > 8 || (opt.slab_mode != QS_SLAB_GATHER && opt.slab_mode != QS_SLAB_REMAP) ||
+        opt.seg_bits < 0 || opt.seg_bits > 8 || opt.merge_bits < 0 || opt.merge_bits > 10 ||
+        (opt.slab_mode != QS_SLAB_GATHER && opt.slab_mode != QS_SLAB_REMAP) ||
         (opt.tc != QS_TC_OFF && opt.tc != QS_TC_TF32X3 && opt.tc != QS_TC_BF16X3) ||
         (opt.dtype != QS_C64 && opt.dtype != QS_C128))
         return fail(QS_EINVAL, "option out of range");
@@ -776,14 +779,16 @@ qs_status qs_plan_dump(const qs_plan *pl, char *buf, size_t cap, size_t *needed)
                         break;
                     }
                     case SB_G1N:
-                    case SB_G1A: {
+                    case SB_G1NM:
+                    case SB_G1A:
+                    case SB_G1AM: {
                         head("DENSE", {reg_phys(sb.j0)}, ctl);
                         out += " m";
                         const cd x = p.coef[sb.mat], y = p.coef[sb.mat + 1], one(1.0);
-                        if (sb.type == SB_G1N) {
-                            cnum(one); cnum(x); cnum(y); cnum(one);
+                        if (sb.type == SB_G1N || sb.type == SB_G1NM) {
+                            cnum(one); cnum(x); cnum(y); cnum(sb.type == SB_G1N ? one : -one);
                         } else {
-                            cnum(x); cnum(one); cnum(one); cnum(y);
+                            cnum(x); cnum(one); cnum(sb.type == SB_G1A ? one : -one); cnum(y);
                         }
                         break;
                     }

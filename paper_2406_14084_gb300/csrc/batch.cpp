@@ -176,11 +176,17 @@ qs_status build(qs_batch *B, int slab_bits, int stage_bits)
         amp_off += uint64_t(1) << B->n[c];
         done0 += (unsigned)C.npass;
     }
+    // Work items: runs of consecutive slabs of one pass of one circuit, listed round by round.
+    // A CTA walks the slabs of a run with its own double buffering, so the queue is read once per
+    // run; runs of up to 8 slabs keep at least 256 items per pass of the largest circuits.
     for (int r = 0; r < rounds; ++r)
         for (int c = 0; c < B->ncirc; ++c)
-            if (B->circs[c].npass > r)
-                for (uint32_t sl = 0; sl < (1u << B->circs[c].nslab_log); ++sl)
-                    B->items.push_back(BatchItem{c, r, sl, 0});
+            if (B->circs[c].npass > r) {
+                const uint32_t ns = 1u << B->circs[c].nslab_log;
+                const uint32_t run = std::max(1u, std::min(8u, ns / 256u));
+                for (uint32_t sl = 0; sl < ns; sl += run)
+                    B->items.push_back(BatchItem{c, r, sl, (int32_t)std::min(run, ns - sl)});
+            }
     B->slab_bits = slab_bits;
     B->stage_bits = B->plans.empty() ? stage_bits : B->plans[0].stage_bits;
     B->b_max = bmax;
@@ -191,7 +197,8 @@ qs_status build(qs_batch *B, int slab_bits, int stage_bits)
     const size_t o_pass = put(h, passes), o_ops = put(h, ops), o_st = put(h, stages), o_sb = put(h, subs);
     const size_t o_circ = put(h, B->circs), o_item = put(h, B->items);
     const size_t o_coef = (h.size() + 255) & ~size_t(255);
-    h.resize(o_coef + std::max<size_t>(16, coef.size() * amp_size(B->dt)), 0);
+    // two spare entries: the register stages read a sub-op's first two coefficients ahead
+    h.resize(o_coef + (coef.size() + 2) * amp_size(B->dt), 0);
     for (size_t i = 0; i < coef.size(); ++i) {
         if (B->dt == QS_C64) {
             float *f = reinterpret_cast<float *>(h.data() + o_coef) + 2 * i;

@@ -46,11 +46,24 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned *p)
     return v;
 }
 
-// Thread 0: take the next item from the queue into slot k.  `block` selects a bounded blocking
-// wait for its dependency (the circuit's previous pass fully stored) or a single check.
-__device__ void take_item(BatchShared &S, int k, const BatchArgs &a)
+// Thread 0: the next slab for slot k after slot `from`: the following slab of the same run
+// (no queue access; its dependency holds as for the run's first slab), or else the next item
+// from the queue, whose dependency (the circuit's previous pass fully stored) is checked once.
+__device__ void take_item(BatchShared &S, int k, const BatchArgs &a, int from)
 {
     BatchSlot &Z = S.slot[k];
+    if (from >= 0) {
+        const BatchSlot &P = S.slot[from];
+        if (P.st == 1 && P.item.count > 1) {
+            Z.item = P.item;
+            Z.item.slab += 1;
+            Z.item.count -= 1;
+            Z.circ = P.circ;
+            Z.pass = P.pass;
+            Z.st = 1;
+            return;
+        }
+    }
     const unsigned it = atomicAdd(a.head, 1u);
     if (it >= a.nitems) {
         Z.st = 0;
@@ -149,7 +162,7 @@ __global__ void __launch_bounds__(NT, 1)
 
     int cur = 0;
     if (tid == 0) {
-        take_item(S, 0, a);
+        take_item(S, 0, a, -1);
         if (S.slot[0].st == 3) wait_item(S, 0, a);
     }
     __syncthreads();
@@ -164,7 +177,7 @@ __global__ void __launch_bounds__(NT, 1)
         BatchSlot &Y = S.slot[nxt];
         C *const sm = bufs + size_t(cur) * buf_elems;
         // take the next item; gather it now if its dependency already holds
-        if (tid == 0) take_item(S, nxt, a);
+        if (tid == 0) take_item(S, nxt, a, cur);
         __syncthreads();
         bool prefetched = false;
         if (Y.st == 1) {
@@ -200,27 +213,50 @@ __global__ void __launch_bounds__(NT, 1)
                 __syncthreads();
             }
             if (last) {
-                // sum over the slab of |a_x|^2 sum_t c_t (-1)^{popcount(x & z_t)}
-                double acc = 0.0;
-                R part = 0;
-                int cnt = 0;
-                const BatchTerm *T = a.terms + Z.circ.term0;
-                const int nt = Z.circ.nterm;
-                for (uint32_t i = tid; i < nsl; i += NT) {
-                    uint64_t x = base | (i & ((1u << lo) - 1));
-                    for (int m = 0; m < nhi; ++m) x |= uint64_t((i >> (lo + m)) & 1u) << Z.pass.hipos[m];
-                    R h = 0;
-                    for (int t = 0; t < nt; ++t) h += (__popcll(x & T[t].zm) & 1) ? -R(T[t].c) : R(T[t].c);
-                    const C v = sm[swz<SW>(i)];
-                    const R p = v.x * v.x + v.y * v.y;
-                    part = fma(p, h, part);
-                    if (++cnt == 32) {
-                        acc += double(part);
-                        part = 0.f;
-                        cnt = 0;
+                // <psi| sum_t c_t Z_t |psi> over the slab.  With x = base | deposit(i) (base: the
+                // bits outside the slab), (-1)^{popcount(x & z_t)} = s_t(base) (-1)^{popcount(i & zl_t)}
+                // where zl_t is z_t on the slab's local bits, so the slab contributes
+                //   sum_t c_t s_t(base) P^(zl_t),   P^(z) = sum_i |a_i|^2 (-1)^{popcount(i & z)},
+                // the Walsh-Hadamard transform of the slab's probabilities, computed in place in
+                // shared memory (state precision) in b butterfly stages.
+                R *pr = reinterpret_cast<R *>(sm);
+                constexpr int kPer = 32;  // slab amplitudes per thread (2^13 / 256, 2^12 / 128 ...)
+                R pv[kPer];
+#pragma unroll
+                for (int k = 0; k < kPer; ++k) {
+                    const uint32_t i = tid + uint32_t(k) * NT;
+                    if (i < nsl) {
+                        const C v = sm[swz<SW>(i)];
+                        pv[k] = v.x * v.x + v.y * v.y;
                     }
                 }
-                acc += double(part);
+                __syncthreads();  // every amplitude has been read: the buffer now holds pr[]
+#pragma unroll
+                for (int k = 0; k < kPer; ++k) {
+                    const uint32_t i = tid + uint32_t(k) * NT;
+                    if (i < nsl) pr[i] = pv[k];
+                }
+                for (int j = 0; j < b; ++j) {
+                    __syncthreads();
+                    const uint32_t low = (1u << j) - 1u;
+                    for (uint32_t q = tid; q < nsl / 2; q += NT) {
+                        const uint32_t i0 = ((q & ~low) << 1) | (q & low), i1 = i0 | (1u << j);
+                        const R u = pr[i0], w = pr[i1];
+                        pr[i0] = u + w;
+                        pr[i1] = u - w;
+                    }
+                }
+                __syncthreads();
+                const BatchTerm *T = a.terms + Z.circ.term0;
+                const int nt = Z.circ.nterm;
+                double acc = 0.0;
+                for (int t = int(tid); t < nt; t += NT) {
+                    const uint64_t zm = T[t].zm;
+                    uint32_t zl = uint32_t(zm) & ((1u << lo) - 1u);
+                    for (int m = 0; m < nhi; ++m) zl |= uint32_t((zm >> Z.pass.hipos[m]) & 1u) << (lo + m);
+                    const double sg = (__popcll(base & zm) & 1) ? -T[t].c : T[t].c;
+                    acc += sg * double(pr[zl]);
+                }
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
                 if ((tid & 31) == 0) S.red[tid >> 5] = acc;
@@ -231,15 +267,19 @@ __global__ void __launch_bounds__(NT, 1)
                     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
                     if (tid == 0) atomicAdd(a.results + Z.item.circ, v);
                 }
-            }
-            constexpr int kLog16 = (sizeof(C) == 8) ? 1 : 0;
-            const int vps_log = lo - kLog16;
-            const uint32_t nvec = 1u << (b - kLog16);
-            C *g = states + Z.circ.amp_off + base;
-            for (uint32_t v = tid; v < nvec; v += NT) {
-                const uint32_t seg = v >> vps_log, w = v & ((1u << vps_log) - 1);
-                const uint64_t so = Z.seg_lo[seg & 63] | Z.seg_hi[(seg >> 6) & 63];
-                st_stream(reinterpret_cast<uint4 *>(g + so) + w, reinterpret_cast<const uint4 *>(sm)[chunk_of<C>(v)]);
+            } else {
+                // the final states are not kept (the batch returns expectation values only), so
+                // the last pass stores nothing
+                constexpr int kLog16 = (sizeof(C) == 8) ? 1 : 0;
+                const int vps_log = lo - kLog16;
+                const uint32_t nvec = 1u << (b - kLog16);
+                C *g = states + Z.circ.amp_off + base;
+                for (uint32_t v = tid; v < nvec; v += NT) {
+                    const uint32_t seg = v >> vps_log, w = v & ((1u << vps_log) - 1);
+                    const uint64_t so = Z.seg_lo[seg & 63] | Z.seg_hi[(seg >> 6) & 63];
+                    st_stream(reinterpret_cast<uint4 *>(g + so) + w,
+                              reinterpret_cast<const uint4 *>(sm)[chunk_of<C>(v)]);
+                }
             }
         }
         __threadfence();

@@ -29,6 +29,9 @@ __device__ int g_qs_device_status;
 
 namespace {
 
+// 16-byte chunks of the largest slab (2^13 complex64 or 2^12 complex128 amplitudes)
+constexpr uint32_t kMaxVec = 4096;
+
 // ------------------------------------------------------------------ the pass kernel
 //
 // Double-buffered pipeline per CTA: while slab i is computed in buffer i&1, the 16-byte
@@ -73,11 +76,20 @@ __global__ void __launch_bounds__(NT, 1)
     }
     __syncthreads();
 
-    C *const buf0 = reinterpret_cast<C *>(smem_raw + ((sizeof(SlabShared) + 127) & ~size_t(127)));
+    // [SlabShared][vector offsets of the slab's 16-byte chunks: kMaxVec x 8 B][buffer 0][buffer 1]
+    uint64_t *const voff = reinterpret_cast<uint64_t *>(smem_raw + ((sizeof(SlabShared) + 127) & ~size_t(127)));
+    C *const buf0 = reinterpret_cast<C *>(reinterpret_cast<unsigned char *>(voff) + kMaxVec * sizeof(uint64_t));
     const uint32_t nsl = 1u << b;
     constexpr int kLog16 = (sizeof(C) == 8) ? 1 : 0;  // log2(amplitudes per 16-byte vector)
     const int vps_log = lo - kLog16;
     const uint32_t nvec = 1u << (b - kLog16);
+    // the global 16-byte-vector offset of chunk v from the slab base is the same for every slab
+    // of the pass: computed once here, one shared-memory load per chunk afterwards
+    for (uint32_t v = tid; v < nvec; v += NT) {
+        const uint32_t seg = v >> vps_log, w = v & ((1u << vps_log) - 1);
+        voff[v] = ((S.seg_lo[seg & 63] | S.seg_hi[(seg >> 6) & 63]) >> kLog16) + w;
+    }
+    __syncthreads();
     const int op_begin = S.pass.op_begin, op_end = S.pass.op_end;
     auto slab_base = [&](uint64_t slab) {
         uint64_t base = slab << lo;
@@ -91,13 +103,17 @@ __global__ void __launch_bounds__(NT, 1)
     auto chunk_of = [](uint32_t v) -> uint32_t {
         return sizeof(C) == 8 ? (swz<1>(v << 1) >> 1) : swz<2>(v);
     };
+    // chunk_of is linear over GF(2) and NT is a power of two above tid, so the chunk of
+    // v = tid + k NT is chunk_of(tid) ^ chunk_of(k NT), the second term a constant per unrolled k
+    const uint32_t ct = chunk_of(tid);
     auto issue_load = [&](uint64_t slab, uint32_t k) {
-        const C *g = state + slab_base(slab);
+        const uint4 *g = reinterpret_cast<const uint4 *>(state + slab_base(slab));
         const uint32_t dst = smem_addr(buf0 + size_t(k) * nsl);
-        for (uint32_t v = tid; v < nvec; v += NT) {
-            const uint32_t seg = v >> vps_log, w = v & ((1u << vps_log) - 1);
-            const uint64_t so = S.seg_lo[seg & 63] | S.seg_hi[(seg >> 6) & 63];
-            cp_async16(dst + 16u * chunk_of(v), reinterpret_cast<const uint4 *>(g + so) + w);
+#pragma unroll
+        for (uint32_t j = 0; j < kMaxVec / NT; ++j) {
+            const uint32_t v = tid + j * NT;
+            if (v >= nvec) break;
+            cp_async16(dst + 16u * (ct ^ chunk_of(j * NT)), g + voff[v]);
         }
         cp_async_commit();
     };
@@ -128,11 +144,12 @@ __global__ void __launch_bounds__(NT, 1)
         }
         // store
         if (!S.pass.has_perm) {
-            for (uint32_t v = tid; v < nvec; v += NT) {
-                const uint32_t seg = v >> vps_log, w = v & ((1u << vps_log) - 1);
-                const uint64_t so = S.seg_lo[seg & 63] | S.seg_hi[(seg >> 6) & 63];
-                st_stream(reinterpret_cast<uint4 *>(gbase + so) + w,
-                          reinterpret_cast<const uint4 *>(sm)[chunk_of(v)]);
+            uint4 *gv = reinterpret_cast<uint4 *>(gbase);
+#pragma unroll
+            for (uint32_t j = 0; j < kMaxVec / NT; ++j) {
+                const uint32_t v = tid + j * NT;
+                if (v >= nvec) break;
+                st_stream(gv + voff[v], reinterpret_cast<const uint4 *>(sm)[ct ^ chunk_of(j * NT)]);
             }
         } else {
             for (uint32_t d = tid; d < nsl; d += NT) {
@@ -179,7 +196,8 @@ int launch_pass_t(const LaunchCtx &c, const PassArgs &a, const DevPass &h, char 
 size_t pass_smem_bytes(qs_dtype dt, int b, int /*lo*/)
 {
     const size_t amp = dt == QS_C64 ? 8 : 16;
-    return ((sizeof(SlabShared) + 127) & ~size_t(127)) + 2 * (amp << b);  // two slab buffers
+    // shared block, chunk-offset table, two slab buffers
+    return ((sizeof(SlabShared) + 127) & ~size_t(127)) + kMaxVec * sizeof(uint64_t) + 2 * (amp << b);
 }
 
 int max_slab_bits(qs_dtype dt)

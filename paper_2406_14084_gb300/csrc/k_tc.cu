@@ -20,6 +20,12 @@
 // overlaps the MMAs, the accumulator read-back and the stores.  The E operand stays in shared
 // memory for the whole launch.  Every mbarrier wait is bounded; on expiry the CTA
 // records QS_ETIMEOUT, releases its tensor memory and exits.
+//
+// TF32 x 3 mode (kind::tf32): the same three products with TF32 parts (10 stored mantissa bits
+// each, so hi + lo carries about 22 bits against BF16's 16).  The 4-byte operands take twice the
+// space, so each slab is multiplied in two K halves of 64 (targets 0..31, then 32..63), both
+// accumulating into the same TMEM columns; the E half-images (hi and lo, 32 KiB each) are copied
+// from global memory (L2-resident) before each half.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -31,7 +37,9 @@ namespace qs {
 namespace {
 
 constexpr int kThreads = 256;  // 8 warps: two per TMEM lane quarter
-constexpr uint32_t kOpBytes = kTcRows * kTcK * 2;  // one BF16 operand: 128 x 128 x 2 = 32 KiB
+// One operand part in shared memory: a BF16 operand (128 x 128 x 2 B), or half the K range of a
+// TF32 operand (128 x 64 x 4 B): 32 KiB either way.
+constexpr uint32_t kOpBytes = kTcRows * kTcK * 2;
 constexpr uint32_t kSlabBytes = (1u << kTcSlabBits) * 8;
 constexpr uint32_t kOffAhi = kSlabBytes, kOffAlo = kOffAhi + kOpBytes, kOffBhi = kOffAlo + kOpBytes,
                    kOffBlo = kOffBhi + kOpBytes, kOffCtl = kOffBlo + kOpBytes;
@@ -55,6 +63,9 @@ __device__ __forceinline__ void cp_async16(uint32_t dst, const void *src)
 }
 
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 __device__ __forceinline__ void cp_async_wait_all()
 {
@@ -99,8 +110,12 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr)
     return d;
 }
 
-// Instruction descriptor, kind::f16: D FP32, A and B BF16, both K-major, M = 128, N = 128.
+// Instruction descriptors: D FP32 (bits 4-5 = 1), A and B both K-major, N = 128 (bits 17-22 hold
+// N / 8), M = 128 (bits 24-28 hold M / 16); operand format in bits 7-9 (A) and 10-12 (B):
+// kind::f16 with BF16 = 1, kind::tf32 with TF32 = 2.
 constexpr uint32_t kIdescBf16 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t(kTcK) >> 3) << 17) |
+                                ((uint32_t(kTcRows) >> 4) << 24);
+constexpr uint32_t kIdescTf32 = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t(kTcK) >> 3) << 17) |
                                 ((uint32_t(kTcRows) >> 4) << 24);
 
 __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accumulate)
@@ -111,6 +126,24 @@ __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64
         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
         "l"(adesc), "l"(bdesc), "r"(kIdescBf16), "r"(accumulate)
         : "memory");
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(kIdescTf32), "r"(accumulate)
+        : "memory");
+}
+
+// TF32 value nearest to x (round to nearest, ties away), as FP32 bits with the low 13 bits clear.
+__device__ __forceinline__ uint32_t to_tf32(float x)
+{
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
 }
 
 __device__ __forceinline__ void mma_commit(uint32_t bar)
@@ -145,8 +178,13 @@ __device__ __forceinline__ uint32_t op_chunk_offset(uint32_t row, uint32_t chunk
     return kb * (kTcRows * 128u) + row * 128u + ((c ^ (row & 7u)) << 4);
 }
 
+// MODE = QS_TC_BF16X3: E_hi / E_lo stay in shared memory for the whole launch and each slab is
+// one GEMM over K = 128.  MODE = QS_TC_TF32X3: the operands are 4-byte TF32, so a slab is two
+// GEMM halves over K = 64 each, and the E half-images are loaded from global memory (L2) for
+// every half.
+template <int MODE>
 __global__ void __launch_bounds__(kThreads, 1)
-    tc_bf16_kernel(float2 *__restrict__ state, const DevTc *__restrict__ d_tc,
+    tc_kernel(float2 *__restrict__ state, const DevTc *__restrict__ d_tc,
                    const unsigned char *__restrict__ images, uint64_t nslabs, int *status)
 {
     extern __shared__ unsigned char smem_raw[];
@@ -167,11 +205,23 @@ __global__ void __launch_bounds__(kThreads, 1)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    // resident E_hi / E_lo images (64 KiB contiguous in global memory)
-    {
-        const unsigned char *src = images + d_tc->img;
+    constexpr bool kTf32 = MODE == QS_TC_TF32X3;
+    constexpr int kParts = kTf32 ? 2 : 1;
+    const unsigned char *img = images + d_tc->img;
+    // E half h of part hi / lo (TF32: [hi h0 | hi h1 | lo h0 | lo h1], 32 KiB each) -> B region
+    auto load_b = [&](int h) {
+        const unsigned char *src_hi = img + h * kOpBytes, *src_lo = img + (2 + h) * kOpBytes;
+        const uint32_t dhi = saddr(base + kOffBhi), dlo = saddr(base + kOffBlo);
+        for (uint32_t v = tid; v < kOpBytes / 16; v += kThreads) {
+            cp_async16(dhi + 16 * v, src_hi + 16 * v);
+            cp_async16(dlo + 16 * v, src_lo + 16 * v);
+        }
+        cp_async_commit();
+    };
+    if (!kTf32) {
+        // resident E_hi / E_lo images (64 KiB contiguous in global memory)
         const uint32_t dst = saddr(base + kOffBhi);
-        for (uint32_t v = tid; v < (2 * kOpBytes) / 16; v += kThreads) cp_async16(dst + 16 * v, src + 16 * v);
+        for (uint32_t v = tid; v < (2 * kOpBytes) / 16; v += kThreads) cp_async16(dst + 16 * v, img + 16 * v);
     }
     tc_fence_before();
     __syncthreads();
@@ -228,59 +278,91 @@ __global__ void __launch_bounds__(kThreads, 1)
     // next slab can stream into the slab buffer while this one is multiplied and stored.
     float2 *res = reinterpret_cast<float2 *>(base + kOffAhi);
     if (uint64_t(blockIdx.x) < nslabs) issue_load(slab_ptr(blockIdx.x));
-    for (uint64_t s = blockIdx.x; s < nslabs; s += gridDim.x) {
+    for (uint64_t s = blockIdx.x; s < nslabs && !failed; s += gridDim.x) {
         float2 *g = slab_ptr(s);
         cp_async_wait_all();
         __syncthreads();
-        // split row m = tid into BF16 hi / lo in the swizzled operand layout (16-byte chunks of 8)
-        {
-            // thread (m, half): row m, 16-byte chunks half*8 .. half*8+7 of its 16
-            const uint32_t m = tid & 127u, mo = K.moff[m], c16b = (tid >> 7) * (kTcK / 16);
+        const bool more = s + gridDim.x < nslabs;
+        for (int h = 0; h < kParts; ++h) {
+            if (kTf32) load_b(h);  // the B region is free: the previous GEMM has completed
+            // split row m into hi / lo in the swizzled operand layout, 16-byte chunks half*8 ..
+            // half*8+7 of the row's 16 (thread (m, half) = (tid % 128, tid / 128))
+            const uint32_t m = tid & 127u, mo = K.moff[m], c16b = (tid >> 7) * 8;
+            if (!kTf32) {
 #pragma unroll 2
-            for (uint32_t c16 = c16b; c16 < c16b + kTcK / 16; ++c16) {
-                __nv_bfloat162 h[4], l[4];
+                for (uint32_t c16 = c16b; c16 < c16b + 8; ++c16) {
+                    __nv_bfloat162 hv[4], lv[4];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const float2 a = slab[mo | K.joff[c16 * 4 + q]];
-                    const __nv_bfloat16 hx = __float2bfloat16_rn(a.x), hy = __float2bfloat16_rn(a.y);
-                    h[q] = __halves2bfloat162(hx, hy);
-                    l[q] = __halves2bfloat162(__float2bfloat16_rn(a.x - __bfloat162float(hx)),
-                                              __float2bfloat16_rn(a.y - __bfloat162float(hy)));
+                    for (int q = 0; q < 4; ++q) {
+                        const float2 a = slab[mo | K.joff[c16 * 4 + q]];
+                        const __nv_bfloat16 hx = __float2bfloat16_rn(a.x), hy = __float2bfloat16_rn(a.y);
+                        hv[q] = __halves2bfloat162(hx, hy);
+                        lv[q] = __halves2bfloat162(__float2bfloat16_rn(a.x - __bfloat162float(hx)),
+                                                   __float2bfloat16_rn(a.y - __bfloat162float(hy)));
+                    }
+                    const uint32_t off = op_chunk_offset(m, c16);
+                    *reinterpret_cast<uint4 *>(base + kOffAhi + off) = *reinterpret_cast<const uint4 *>(hv);
+                    *reinterpret_cast<uint4 *>(base + kOffAlo + off) = *reinterpret_cast<const uint4 *>(lv);
                 }
-                const uint32_t off = op_chunk_offset(m, c16);
-                *reinterpret_cast<uint4 *>(base + kOffAhi + off) = *reinterpret_cast<const uint4 *>(h);
-                *reinterpret_cast<uint4 *>(base + kOffAlo + off) = *reinterpret_cast<const uint4 *>(l);
+            } else {
+                // K half h holds targets j = 32h .. 32h + 31; a chunk is 2 amplitudes (re, im, re, im)
+#pragma unroll 2
+                for (uint32_t c16 = c16b; c16 < c16b + 8; ++c16) {
+                    const uint32_t j = 32u * uint32_t(h) + 2u * c16;
+                    const float2 a0 = slab[mo | K.joff[j]], a1 = slab[mo | K.joff[j + 1]];
+                    const float xs[4] = {a0.x, a0.y, a1.x, a1.y};
+                    uint32_t hv[4], lv[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        hv[q] = to_tf32(xs[q]);
+                        lv[q] = to_tf32(xs[q] - __uint_as_float(hv[q]));
+                    }
+                    const uint32_t off = op_chunk_offset(m, c16);
+                    *reinterpret_cast<uint4 *>(base + kOffAhi + off) = make_uint4(hv[0], hv[1], hv[2], hv[3]);
+                    *reinterpret_cast<uint4 *>(base + kOffAlo + off) = make_uint4(lv[0], lv[1], lv[2], lv[3]);
+                }
             }
-        }
-        fence_proxy_async();
-        __syncthreads();
-        // the slab buffer has been read: prefetch this CTA's next slab into it
-        if (s + gridDim.x < nslabs) issue_load(slab_ptr(s + gridDim.x));
-        if (tid == 0) {
+            const bool last = h == kParts - 1;
+            if (last) {
+                __syncthreads();  // every split has read the slab buffer
+                // prefetch this CTA's next slab into it; it lands while the GEMM runs
+                if (more) issue_load(slab_ptr(s + gridDim.x));
+            }
+            if (kTf32) {
+                // the B half (committed before the prefetch) must have landed
+                if (last && more) cp_async_wait<1>();
+                else cp_async_wait<0>();
+            }
+            fence_proxy_async();
+            __syncthreads();
+            if (tid == 0) {
+                tc_fence_after();
+                // D (+)= A_hi E_hi^T + A_hi E_lo^T + A_lo E_hi^T over 8 K-steps of 32 bytes
+                const uint32_t ops[3][2] = {{sAhi, sBhi}, {sAhi, sBlo}, {sAlo, sBhi}};
+#pragma unroll
+                for (int pr = 0; pr < 3; ++pr)
+#pragma unroll
+                    for (int ks = 0; ks < 8; ++ks) {
+                        const uint32_t koff = (uint32_t(ks) >> 2) * (kTcRows * 128u) + (uint32_t(ks) & 3u) * 32u;
+                        const uint32_t acc = (h | pr | ks) ? 1u : 0u;
+                        if (kTf32) mma_tf32(tmem, smem_desc(ops[pr][0] + koff), smem_desc(ops[pr][1] + koff), acc);
+                        else mma_bf16(tmem, smem_desc(ops[pr][0] + koff), smem_desc(ops[pr][1] + koff), acc);
+                    }
+                mma_commit(bar);
+            }
+            const bool ok = mbar_wait_bounded(bar, phase);
+            phase ^= 1u;
+            if (__syncthreads_or(!ok)) {
+                if (tid == 0) atomicExch(status, QS_ETIMEOUT);
+                mbar_wait_bounded(bar, phase ^ 1u);  // bounded grace for the MMAs in flight
+                failed = true;
+                break;
+            }
             tc_fence_after();
-            // D = A_hi E_hi^T + A_hi E_lo^T + A_lo E_hi^T over 8 K-steps of 16 elements
-            const uint32_t ops[3][2] = {{sAhi, sBhi}, {sAhi, sBlo}, {sAlo, sBhi}};
-#pragma unroll
-            for (int pr = 0; pr < 3; ++pr)
-#pragma unroll
-                for (int ks = 0; ks < kTcK / 16; ++ks) {
-                    const uint32_t koff = (uint32_t(ks) >> 2) * (kTcRows * 128u) + (uint32_t(ks) & 3u) * 32u;
-                    mma_bf16(tmem, smem_desc(ops[pr][0] + koff), smem_desc(ops[pr][1] + koff),
-                             (pr | ks) ? 1u : 0u);
-                }
-            mma_commit(bar);
         }
-        const bool ok = mbar_wait_bounded(bar, phase);
-        phase ^= 1u;
-        if (__syncthreads_or(!ok)) {
-            if (tid == 0) atomicExch(status, QS_ETIMEOUT);
-            mbar_wait_bounded(bar, phase ^ 1u);  // bounded grace for the MMAs in flight
-            failed = true;
-            break;
-        }
-        tc_fence_after();
+        if (failed) break;
         // epilogue: warp w reads rows 32q..32q+31 of its TMEM lane quarter q = w % 4, columns
-        // 64h..64h+63 with h = w / 4, 32 columns at a time
+        // 64h..64h+63 with h = w / 4, 32 columns at a time, into the free operand region
         {
             const uint32_t q4 = warp & 3u, m = q4 * 32 + lane, mo = K.moff[m], cb = (warp >> 2) * (kTcK / 2);
 #pragma unroll 1
@@ -312,29 +394,24 @@ __global__ void __launch_bounds__(kThreads, 1)
 
 }  // namespace
 
-size_t tc_image_bytes(int /*mode*/) { return 2 * size_t(kOpBytes); }
+size_t tc_image_bytes(int mode) { return (mode == QS_TC_TF32X3 ? 4 : 2) * size_t(kOpBytes); }
 
-
-
-int launch_tc(const LaunchCtx &c, const DevTc *d_tc, const DevTc &h, const void *d_images, char *err,
-              size_t errlen)
+namespace {
+template <int MODE>
+int launch_tc_t(const LaunchCtx &c, const DevTc *d_tc, const void *d_images, char *err, size_t errlen)
 {
-    if (c.dt != QS_C64 || h.mode != QS_TC_BF16X3) {
-        snprintf(err, errlen, "tensor-core path: only complex64 with BF16x3 splitting is built");
-        return QS_EUNSUPPORTED;
-    }
     const size_t smem = kOffCtl + sizeof(TcCtl) + 1024;
     static int attr_dev = -1;
     int dev = 0;
     cudaGetDevice(&dev);
     if (attr_dev != dev) {
-        cudaFuncSetAttribute(tc_bf16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(tc_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         attr_dev = dev;
     }
     const uint64_t nslabs = 1ull << (c.n - kTcSlabBits);
     uint64_t grid = uint64_t(num_sms());
     if (grid > nslabs) grid = nslabs;
-    tc_bf16_kernel<<<(unsigned)grid, kThreads, smem, (cudaStream_t)c.stream>>>(
+    tc_kernel<MODE><<<(unsigned)grid, kThreads, smem, (cudaStream_t)c.stream>>>(
         reinterpret_cast<float2 *>(c.amp), d_tc, reinterpret_cast<const unsigned char *>(d_images), nslabs,
         device_status_ptr());
     cudaError_t e = cudaGetLastError();
@@ -343,6 +420,20 @@ int launch_tc(const LaunchCtx &c, const DevTc *d_tc, const DevTc &h, const void 
         return QS_ECUDA;
     }
     return QS_OK;
+}
+}  // namespace
+
+int launch_tc(const LaunchCtx &c, const DevTc *d_tc, const DevTc &h, const void *d_images, char *err,
+              size_t errlen)
+{
+    if (c.dt != QS_C64) {
+        snprintf(err, errlen, "tensor-core path: complex64 states only");
+        return QS_EUNSUPPORTED;
+    }
+    if (h.mode == QS_TC_BF16X3) return launch_tc_t<QS_TC_BF16X3>(c, d_tc, d_images, err, errlen);
+    if (h.mode == QS_TC_TF32X3) return launch_tc_t<QS_TC_TF32X3>(c, d_tc, d_images, err, errlen);
+    snprintf(err, errlen, "tensor-core path: unknown mode %d", h.mode);
+    return QS_EINVAL;
 }
 
 }  // namespace qs

@@ -73,6 +73,8 @@ void tally_sub(const DevSub &sb, float *f)
         break;
     case SB_G1N:
     case SB_G1A:
+    case SB_G1NM:
+    case SB_G1AM:
         f[17] += 1;
         f[26] += float(2.0 * act);
         f[27] = std::max(f[27], 1.f);

@@ -604,22 +604,24 @@ bool controlled_phase(const CGate &g, cd &phase)
 // includes slab bits outside the registers or physical bits outside the slab joins too: those
 // bits are constant for a thread's group, so they index the table (up to kMergeCondBits of them
 // per table).  Diagonal tables that already read such bits stay where they are.
-constexpr int kMergeCondBits = 6;  // condition bits of one merged table (2^(RB + 6) entries at most)
+constexpr int kMergeCondBitsDefault = 6;  // condition bits of one merged table (2^(RB + 6) entries)
 
 void merge_stage_diagonals(Plan &plan, int s0, int RB, Coefs &cf)
 {
+    const int kMergeCondBits = plan.opt.merge_bits > 0 ? std::min(plan.opt.merge_bits, 10) : kMergeCondBitsDefault;
     const int E = 1 << RB;
     std::vector<DevSub> in(plan.subs.begin() + s0, plan.subs.end());
     const int ns = (int)in.size();
     auto target_bits = [](const DevSub &s) -> uint32_t {
         switch (s.type) {
-        case SB_G1: case SB_G1R: case SB_G1N: case SB_G1A: case SB_X: return 1u << s.j0;
+        case SB_G1: case SB_G1R: case SB_G1N: case SB_G1A: case SB_G1NM: case SB_G1AM: case SB_X:
+            return 1u << s.j0;
         case SB_G2: case SB_SWAP: return (1u << s.j0) | (1u << s.j1);
         default: return 0;
         }
     };
     auto is_diag = [](const DevSub &s) { return s.type == SB_PHASE || s.type == SB_DIAG; };
-    auto eligible = [](const DevSub &s) {
+    auto eligible = [kMergeCondBits](const DevSub &s) {
         return (s.type == SB_PHASE && __builtin_popcount(s.lcm) + __builtin_popcountll(s.ocm) <= kMergeCondBits) ||
                (s.type == SB_DIAG && s.ndl == 0);
     };
@@ -743,14 +745,14 @@ void merge_stage_diagonals(Plan &plan, int s0, int RB, Coefs &cf)
     plan.subs.insert(plan.subs.end(), out.begin(), out.end());
 }
 
-// Write each uncontrolled real 2x2 sub M of a stage (rotations, H) as M = D N, where N has two
-// unit entries -- N = [[1, m01/m00], [m10/m11, 1]] with D = diag(m00, m11) when |m00| >= |m01|,
-// else N = [[m00/m01, 1], [1, m11/m10]] with D = diag(m01, m10) -- so that N costs one FMA per
-// real output instead of two, and every ratio is at most 1 in magnitude.  For an orthogonal M,
-// |d1| = |d0|: D = d0 diag(1, d1/d0) with d1/d0 = +-1.  The sign becomes a phase sub on the target
-// bit right after N, and the real scalars d0 of all factored subs are collected into one scalar
-// sub of the stage (a diagonal that reads no bit); the diagonal merge that follows folds both
-// into the stage's tables where that pays.  The matrices stay FP64 products of the gate's own
+// Write each uncontrolled real 2x2 sub M of a stage (rotations, reflections such as H) as a real
+// scalar times a matrix N with two entries of magnitude 1, so that N costs one FMA per real
+// output instead of two.  For an orthogonal M (|m00| = |m11|, |m01| = |m10|):
+//   |m00| >= |m01|:  M = m00 [[1, m01/m00], [m10/m00, m11/m00]],  m11/m00 = +1 or -1  (N, NM)
+//   otherwise:       M = m01 [[m00/m01, 1], [m10/m01, m11/m01]],  m10/m01 = +1 or -1  (A, AM)
+// so every ratio is at most 1 in magnitude.  The scalars of all factored subs are collected into
+// one scalar sub of the stage (a diagonal that reads no bit), which the diagonal merge that
+// follows folds into a table where one exists.  The matrices are FP64 ratios of the gate's own
 // entries (Eq. 2-3 reassociated), so results change only by rounding.
 void factor_stage_rotations(Plan &plan, int s0, Coefs &cf)
 {
@@ -762,7 +764,8 @@ void factor_stage_rotations(Plan &plan, int s0, Coefs &cf)
         if (sb.type == SB_G1R && !(sb.scm | sb.lcm | sb.ocm)) ++cand;
         if (sb.type == SB_PHASE || sb.type == SB_DIAG) has_diag = true;
     }
-    // the stage scalar costs one multiply per amplitude unless a table absorbs it
+    // the stage scalar costs one multiply per amplitude unless a table absorbs it, the same as
+    // the FMA one factored sub saves
     if (cand == 0 || (cand < 2 && !has_diag)) return;
     double sigma = 1.0;
     std::vector<DevSub> out;
@@ -775,35 +778,30 @@ void factor_stage_rotations(Plan &plan, int s0, Coefs &cf)
         const double m00 = plan.coef[sb.mat].real(), m01 = plan.coef[sb.mat + 1].real();
         const double m10 = plan.coef[sb.mat + 2].real(), m11 = plan.coef[sb.mat + 3].real();
         DevSub f = sb;
-        double x, y, d0, d1;
+        double x, y, d;
+        bool unit;  // the entry that must be +-1 is, to rounding
         if (std::abs(m00) >= std::abs(m01)) {
-            f.type = SB_G1N;
-            d0 = m00;
-            d1 = m11;
-            x = m01 / m00;
-            y = d1 != 0.0 ? m10 / m11 : 0.0;
+            d = m00;
+            const double r = d != 0.0 ? m11 / d : 0.0;
+            unit = std::abs(std::abs(r) - 1.0) <= 1e-13;
+            f.type = r > 0 ? SB_G1N : SB_G1NM;
+            x = d != 0.0 ? m01 / d : 0.0;
+            y = d != 0.0 ? m10 / d : 0.0;
         } else {
-            f.type = SB_G1A;
-            d0 = m01;
-            d1 = m10;
-            x = m00 / m01;
-            y = d1 != 0.0 ? m11 / m10 : 0.0;
+            d = m01;
+            const double r = m10 / d;
+            unit = std::abs(std::abs(r) - 1.0) <= 1e-13;
+            f.type = r > 0 ? SB_G1A : SB_G1AM;
+            x = m00 / d;
+            y = m11 / d;
         }
-        if (d0 == 0.0 || std::abs(std::abs(d1) - std::abs(d0)) > 1e-12 * std::abs(d0)) {
+        if (d == 0.0 || !unit) {
             out.push_back(sb);  // not orthogonal: keep the full matrix
             continue;
         }
         f.mat = cf.push(std::vector<cd>{cd(x), cd(y)});
         out.push_back(f);
-        sigma *= d0;
-        if ((d1 < 0) != (d0 < 0)) {
-            DevSub sg;
-            std::memset(&sg, 0, sizeof sg);
-            sg.type = SB_PHASE;
-            sg.scm = 1u << sb.j0;
-            sg.mat = cf.push(std::vector<cd>{cd(-1.0)});
-            out.push_back(sg);
-        }
+        sigma *= d;
     }
     DevSub sc;
     std::memset(&sc, 0, sizeof sc);
@@ -1065,6 +1063,52 @@ float bf16_value(uint16_t h)
 // E = E_hi + E_lo in BF16 (from FP64), each stored in the 128-byte-swizzled K-major layout
 // (K split into 128-byte atoms of 64 elements stored one after the other for all 128 rows;
 // 16-byte chunk c of row r placed at chunk c ^ (r & 7)).
+// TF32 value nearest to f (round to nearest even on the 10 stored mantissa bits), as FP32 bits.
+uint32_t tf32_rne(float f)
+{
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    u += 0xFFFu + ((u >> 13) & 1u);
+    return u & ~0x1FFFu;
+}
+
+float tf32_value(uint32_t u)
+{
+    float f;
+    std::memcpy(&f, &u, 4);
+    return f;
+}
+
+// TF32 x 3 images: E = E_hi + E_lo in TF32 (from FP64), 4-byte elements in the same swizzled
+// K-major layout with 128-byte atoms of 32 elements; per part the four K atoms follow each other,
+// so K half h (atoms 2h, 2h + 1) is one contiguous 32 KiB block.  Order: hi, then lo.
+void tc_images_tf32(const std::vector<cd> &U, std::vector<unsigned char> &out)
+{
+    const int K = kTcK, R = kTcK;
+    std::vector<uint32_t> hi(size_t(R) * K), lo(size_t(R) * K);
+    for (int j = 0; j < K / 2; ++j)
+        for (int l = 0; l < K / 2; ++l) {
+            const cd u = U[size_t(j) * (K / 2) + l];
+            const double e[2][2] = {{u.real(), -u.imag()}, {u.imag(), u.real()}};
+            for (int a = 0; a < 2; ++a)
+                for (int c = 0; c < 2; ++c) {
+                    const int n = 2 * j + a, k = 2 * l + c;
+                    const double x = e[a][c];
+                    const uint32_t h = tf32_rne((float)x);
+                    const uint32_t w = tf32_rne((float)(x - (double)tf32_value(h)));
+                    const size_t kb = size_t(k) >> 5, kin = size_t(k) & 31;
+                    const size_t chunk = kin >> 2, within = kin & 3;
+                    const size_t idx = kb * (size_t(R) * 32) + size_t(n) * 32 + ((chunk ^ (n & 7)) << 2) + within;
+                    hi[idx] = h;
+                    lo[idx] = w;
+                }
+        }
+    const size_t base = out.size();
+    out.resize(base + 2 * hi.size() * 4);
+    std::memcpy(out.data() + base, hi.data(), hi.size() * 4);
+    std::memcpy(out.data() + base + hi.size() * 4, lo.data(), lo.size() * 4);
+}
+
 void tc_images(const std::vector<cd> &U, std::vector<unsigned char> &out)
 {
     const int K = kTcK, R = kTcK;
@@ -1125,7 +1169,8 @@ void emit_tc(Plan &plan, const CGate &g, const std::vector<int> &phys, int lo, i
         if (!(tmask >> l & 1)) T.mpos[m++] = (uint8_t)l;
     T.img = (uint32_t)plan.tc_images.size();
     T.mode = mode;
-    tc_images(g.m, plan.tc_images);
+    if (mode == QS_TC_TF32X3) tc_images_tf32(g.m, plan.tc_images);
+    else tc_images(g.m, plan.tc_images);
     plan.tc_coef.push_back((uint32_t)plan.coef.size());
     plan.coef.insert(plan.coef.end(), g.m.begin(), g.m.end());
     plan.tc_phys.push_back(tphys);
@@ -1318,9 +1363,9 @@ int build_plan(const std::vector<CGate> &gates_in, int n, qs_dtype dt, const qs_
             err = "the tensor-core path is built for complex64 states";
             return QS_EUNSUPPORTED;
         }
-        if (opt.tc != QS_TC_BF16X3) {
-            err = "tensor-core mode: only BF16x3 splitting is built";
-            return QS_EUNSUPPORTED;
+        if (opt.tc != QS_TC_BF16X3 && opt.tc != QS_TC_TF32X3) {
+            err = "unknown tensor-core mode";
+            return QS_EINVAL;
         }
         if (n < kTcSlabBits || !opt.blocking) {
             err = "the tensor-core path needs blocking and at least 13 qubits";

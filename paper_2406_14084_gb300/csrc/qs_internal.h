@@ -78,6 +78,8 @@ enum SubType : uint8_t {
     SB_G1R = 6,    // 2x2 matrix with real entries on register bit j0
     SB_G1N = 7,    // real [[1, x], [y, 1]] on register bit j0 (coef[mat] = x, coef[mat + 1] = y)
     SB_G1A = 8,    // real [[x, 1], [1, y]] on register bit j0 (coef[mat] = x, coef[mat + 1] = y)
+    SB_G1NM = 9,   // real [[1, x], [y, -1]] on register bit j0
+    SB_G1AM = 10,  // real [[x, 1], [-1, y]] on register bit j0
 };
 
 // 48 bytes, 16-byte aligned: the kernels fetch the first 24 bytes with one 16-byte and one
@@ -165,8 +167,8 @@ struct BatchCirc {
 };
 struct BatchItem {
     int32_t circ, pass;
-    uint32_t slab;
-    int32_t pad;
+    uint32_t slab;      // first slab of the run
+    int32_t count;      // consecutive slabs in the run (>= 1)
 };
 struct BatchTerm {
     uint64_t zm;        // physical Z mask

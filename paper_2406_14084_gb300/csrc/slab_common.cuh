@@ -34,6 +34,50 @@ __device__ __forceinline__ void st_stream(uint4 *p, uint4 v)
 
 // ------------------------------------------------------------------ register sub-ops
 
+// s * b + a on both parts of a complex amplitude with a real scalar s.  Complex64 uses one packed
+// fma.rn.f32x2 (two FP32 FMAs in one instruction); complex128 two FP64 FMAs.
+__device__ __forceinline__ float2 rfma(float s, float2 b, float2 a)
+{
+    float2 d;
+    asm("{\n\t.reg .b64 rs, rb, ra, rd;\n\t"
+        "mov.b64 rs, {%2, %2};\n\t"
+        "mov.b64 rb, {%3, %4};\n\t"
+        "mov.b64 ra, {%5, %6};\n\t"
+        "fma.rn.f32x2 rd, rs, rb, ra;\n\t"
+        "mov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(s), "f"(b.x), "f"(b.y), "f"(a.x), "f"(a.y));
+    return d;
+}
+__device__ __forceinline__ double2 rfma(double s, double2 b, double2 a)
+{
+    return make_double2(fma(s, b.x, a.x), fma(s, b.y, a.y));
+}
+// s * b on both parts (packed mul.rn.f32x2 for complex64).
+__device__ __forceinline__ float2 rmul(float s, float2 b)
+{
+    float2 d;
+    asm("{\n\t.reg .b64 rs, rb, rd;\n\t"
+        "mov.b64 rs, {%2, %2};\n\t"
+        "mov.b64 rb, {%3, %4};\n\t"
+        "mul.rn.f32x2 rd, rs, rb;\n\t"
+        "mov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(s), "f"(b.x), "f"(b.y));
+    return d;
+}
+__device__ __forceinline__ double2 rmul(double s, double2 b) { return make_double2(s * b.x, s * b.y); }
+// s * b - a on both parts (scalar FMAs: the negation folds into the FMA's operand).
+__device__ __forceinline__ float2 rfms(float s, float2 b, float2 a)
+{
+    return make_float2(fmaf(s, b.x, -a.x), fmaf(s, b.y, -a.y));
+}
+__device__ __forceinline__ double2 rfms(double s, double2 b, double2 a)
+{
+    return make_double2(fma(s, b.x, -a.x), fma(s, b.y, -a.y));
+}
+
+
 template <typename C, int RB, int J, bool CTL>
 __device__ __forceinline__ void sub_g1_impl(C (&v)[1 << RB], const C *__restrict__ M, uint32_t scm)
 {
@@ -103,10 +147,7 @@ __device__ __forceinline__ void sub_phase_mask(C (&v)[1 << RB], C p, bool neg, b
     } else if (real) {
 #pragma unroll
         for (int e = 0; e < (1 << RB); ++e)
-            if ((e & MASK) == MASK) {
-                v[e].x *= p.x;
-                v[e].y *= p.x;
-            }
+            if ((e & MASK) == MASK) v[e] = rmul(p.x, v[e]);
     } else {
 #pragma unroll
         for (int e = 0; e < (1 << RB); ++e)
@@ -125,10 +166,8 @@ __device__ __forceinline__ void sub_g1r_impl(C (&v)[1 << RB], const C *__restric
         if (CTL && (uint32_t(e) & scm) != scm) continue;
         const int e1 = e | (1 << J);
         const C a = v[e], b = v[e1];
-        v[e].x = fma(m01, b.x, m00 * a.x);
-        v[e].y = fma(m01, b.y, m00 * a.y);
-        v[e1].x = fma(m11, b.x, m10 * a.x);
-        v[e1].y = fma(m11, b.y, m10 * a.y);
+        v[e] = rfma(m01, b, rmul(m00, a));
+        v[e1] = rfma(m11, b, rmul(m10, a));
     }
 }
 
@@ -139,41 +178,45 @@ __device__ __forceinline__ void sub_g1r(C (&v)[1 << RB], const C *__restrict__ M
     else sub_g1r_impl<C, RB, J, true>(v, M, scm);
 }
 
-// Real 2x2 with two unit entries, uncontrolled: one FMA per real output.
-//   ANTI = false: [[1, x], [y, 1]]: a' = a + x b, b' = y a + b
-//   ANTI = true:  [[x, 1], [1, y]]: a' = x a + b, b' = a + y b
-template <typename C, int RB, int J, bool ANTI>
-__device__ __forceinline__ void sub_g1n(C (&v)[1 << RB], const C *__restrict__ M)
+// Real 2x2 with two entries of magnitude 1, uncontrolled: one FMA per real output.
+//   K = 0 (SB_G1N):  [[1, x], [y,  1]]: a' = a + x b, b' = y a + b
+//   K = 1 (SB_G1NM): [[1, x], [y, -1]]: a' = a + x b, b' = y a - b
+//   K = 2 (SB_G1A):  [[x, 1], [1,  y]]: a' = x a + b, b' = a + y b
+//   K = 3 (SB_G1AM): [[x, 1], [-1, y]]: a' = x a + b, b' = y b - a
+template <typename C, int RB, int J, int K, typename R>
+__device__ __forceinline__ void sub_g1n(C (&v)[1 << RB], R x, R y)
 {
-    const auto x = M[0].x, y = M[1].x;
 #pragma unroll
     for (int e = 0; e < (1 << RB); ++e) {
         if (e & (1 << J)) continue;
         const int e1 = e | (1 << J);
         const C a = v[e], b = v[e1];
-        if (ANTI) {
-            v[e].x = fma(x, a.x, b.x);
-            v[e].y = fma(x, a.y, b.y);
-            v[e1].x = fma(y, b.x, a.x);
-            v[e1].y = fma(y, b.y, a.y);
+        if (K == 0) {
+            v[e] = rfma(x, b, a);
+            v[e1] = rfma(y, a, b);
+        } else if (K == 1) {
+            v[e] = rfma(x, b, a);
+            v[e1] = rfms(y, a, b);
+        } else if (K == 2) {
+            v[e] = rfma(x, a, b);
+            v[e1] = rfma(y, b, a);
         } else {
-            v[e].x = fma(x, b.x, a.x);
-            v[e].y = fma(x, b.y, a.y);
-            v[e1].x = fma(y, a.x, b.x);
-            v[e1].y = fma(y, a.y, b.y);
+            v[e] = rfma(x, a, b);
+            v[e1] = rfms(y, b, a);
         }
     }
 }
 
-template <typename C, int RB, bool ANTI>
-__device__ __forceinline__ void sub_g1n_j(C (&v)[1 << RB], const C *__restrict__ M, uint32_t j0)
+// x, y: the two free entries (real), read ahead with the sub-op's descriptor.
+template <typename C, int RB, int K, typename R>
+__device__ __forceinline__ void sub_g1n_j(C (&v)[1 << RB], R x, R y, uint32_t j0)
 {
     switch (j0) {
-    case 0: sub_g1n<C, RB, 0, ANTI>(v, M); break;
-    case 1: sub_g1n<C, RB, 1, ANTI>(v, M); break;
-    case 2: sub_g1n<C, RB, 2, ANTI>(v, M); break;
-    case 3: sub_g1n<C, RB, 3, ANTI>(v, M); break;
-    case 4: if (RB > 4) sub_g1n<C, RB, (RB > 4 ? 4 : 0), ANTI>(v, M); break;
+    case 0: sub_g1n<C, RB, 0, K>(v, x, y); break;
+    case 1: sub_g1n<C, RB, 1, K>(v, x, y); break;
+    case 2: sub_g1n<C, RB, 2, K>(v, x, y); break;
+    case 3: sub_g1n<C, RB, 3, K>(v, x, y); break;
+    case 4: if (RB > 4) sub_g1n<C, RB, (RB > 4 ? 4 : 0), K>(v, x, y); break;
     default: break;
     }
 }
@@ -223,9 +266,12 @@ __device__ __forceinline__ SubHead load_sub_head(const DevSub *__restrict__ p)
     return SubHead{a.x, a.y, a.z, a.w, o};
 }
 
+// c0, c1: coef[h.mat] and coef[h.mat + 1], read together with the descriptor one sub-op ahead
+// (the pool carries two spare entries past its end).
 template <typename C, int RB>
 __device__ __forceinline__ void apply_sub(C (&v)[1 << RB], const SubHead &h, const DevSub *__restrict__ sp,
-                                          uint32_t gbase, uint64_t cta_base, const C *__restrict__ coef)
+                                          uint32_t gbase, uint64_t cta_base, const C *__restrict__ coef,
+                                          C c0, C c1)
 {
     if ((gbase & h.lcm) != h.lcm || (cta_base & h.ocm) != h.ocm) return;
     const C *__restrict__ M = coef + h.mat;
@@ -287,7 +333,7 @@ __device__ __forceinline__ void apply_sub(C (&v)[1 << RB], const SubHead &h, con
         // register bits (Z/S/T/P, CZ/CP) get compile-time element lists, so no arithmetic is
         // issued for the untouched elements (predicated-off FP64 work still occupies the
         // narrow FP64 pipe).
-        const C p = M[0];
+        const C p = c0;
         const bool neg = (p.x == -1 && p.y == 0);
         const int pc = __popc(scm);
         if (pc == 0) {
@@ -332,8 +378,10 @@ __device__ __forceinline__ void apply_sub(C (&v)[1 << RB], const SubHead &h, con
         default: break;
         }
         break;
-    case SB_G1N: sub_g1n_j<C, RB, false>(v, M, j0); break;
-    case SB_G1A: sub_g1n_j<C, RB, true>(v, M, j0); break;
+    case SB_G1N: sub_g1n_j<C, RB, 0>(v, c0.x, c1.x, j0); break;
+    case SB_G1NM: sub_g1n_j<C, RB, 1>(v, c0.x, c1.x, j0); break;
+    case SB_G1A: sub_g1n_j<C, RB, 2>(v, c0.x, c1.x, j0); break;
+    case SB_G1AM: sub_g1n_j<C, RB, 3>(v, c0.x, c1.x, j0); break;
     case SB_DIAG: {
         uint32_t hi = 0;
         for (int j = 0; j < int(ndl); ++j) {
@@ -382,30 +430,37 @@ __device__ __noinline__ void run_stage(C *sm, const DevStage *__restrict__ stg,
         }
         const uint32_t pb = swz<SW>(base);
         C v[E];
-        // visit the elements in Gray-code order: one XOR of the address per element
+        // element addresses: the address of e is that of e without its lowest set bit, XORed
+        // with that bit's offset -- a tree of depth popcount(e), so the loads issue back to back
         {
-            uint32_t a = pb;
+            uint32_t a[E];
+            a[0] = pb;
 #pragma unroll
-            for (int i = 0; i < E; ++i) {
-                if (i) a ^= bo[lowest_bit(i)];
-                v[i ^ (i >> 1)] = sm[a];
-            }
+            for (int e = 1; e < E; ++e) a[e] = a[e & (e - 1)] ^ bo[lowest_bit(e)];
+#pragma unroll
+            for (int e = 0; e < E; ++e) v[e] = sm[a[e]];
         }
         if (s0 < s1) {
             SubHead nxt = load_sub_head(subs + s0);
+            C n0 = __ldg(coef + nxt.mat), n1 = __ldg(coef + nxt.mat + 1);
             for (int s = s0; s < s1; ++s) {
                 const SubHead cur = nxt;
-                if (s + 1 < s1) nxt = load_sub_head(subs + s + 1);
-                apply_sub<C, RB>(v, cur, subs + s, base, cta_base, coef);
+                const C c0 = n0, c1 = n1;
+                if (s + 1 < s1) {
+                    nxt = load_sub_head(subs + s + 1);
+                    n0 = __ldg(coef + nxt.mat);
+                    n1 = __ldg(coef + nxt.mat + 1);
+                }
+                apply_sub<C, RB>(v, cur, subs + s, base, cta_base, coef, c0, c1);
             }
         }
         {
-            uint32_t a = pb;
+            uint32_t a[E];
+            a[0] = pb;
 #pragma unroll
-            for (int i = 0; i < E; ++i) {
-                if (i) a ^= bo[lowest_bit(i)];
-                sm[a] = v[i ^ (i >> 1)];
-            }
+            for (int e = 1; e < E; ++e) a[e] = a[e & (e - 1)] ^ bo[lowest_bit(e)];
+#pragma unroll
+            for (int e = 0; e < E; ++e) sm[a[e]] = v[e];
         }
     }
 }

@@ -55,7 +55,7 @@ class QsOptions(ctypes.Structure):
                 ("diag_bits", ctypes.c_int32), ("dtype", ctypes.c_int32),
                 ("stage_bits", ctypes.c_int32), ("fuse_force", ctypes.c_int32),
                 ("euler", ctypes.c_int32), ("factor", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 1)]
+                ("merge_bits", ctypes.c_int32)]
 
 
 class QsPlanInfo(ctypes.Structure):

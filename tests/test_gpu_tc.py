@@ -81,3 +81,40 @@ def test_layered_24_qubits_on_tensor_cores():
     assert st["tc_gates"] >= 4
     assert infidelity(want, got) <= 1e-6
     assert np.max(np.abs(got - want)) <= 1e-5
+
+
+@pytest.mark.parametrize("targets", [(0, 1, 2, 3, 4, 5), (13, 2, 9, 0, 7, 4)])
+def test_tf32x3_single_unitary(targets):
+    """TF32 x 3 mode: two K halves per slab, E half-images loaded per half."""
+    n = 16
+    U = W.random_unitary(6, 7 + sum(targets))
+    gates = [Gate("UNITARY", targets, (), (), U)]
+    init = rand_state(n, 4)
+    want = oracle.apply_circuit(n, gates, init.copy())
+    s = qs.State(n, qs.QS_C64)
+    try:
+        qs.qs_copy_from_host(s.h, init.astype(np.complex64))
+        s.apply(gates, qs.options(tc=qs.QS_TC_TF32X3, dtype=qs.QS_C64))
+        assert qs.qs_stats(s.h)["tc_gates"] == 1
+        got = s.amplitudes().astype(np.complex128)
+    finally:
+        s.close()
+    assert infidelity(want, got) <= 1e-6
+    # TF32 parts carry more bits than BF16 ones: the error is at the complex64 rounding level
+    assert np.max(np.abs(got - want)) <= 2e-6
+
+
+@pytest.mark.parametrize("n,depth", [(17, 8), (24, 4)])
+def test_tf32x3_layered_against_oracle(n, depth):
+    gates = W.layered(n, depth, 1003)
+    init = oracle.basis_state(n, 0)
+    want = oracle.apply_circuit(n, gates, init.copy())
+    s = qs.State(n, qs.QS_C64)
+    try:
+        s.apply(gates, qs.options(tc=qs.QS_TC_TF32X3, dtype=qs.QS_C64))
+        assert qs.qs_stats(s.h)["tc_gates"] > 0
+        got = s.amplitudes().astype(np.complex128)
+    finally:
+        s.close()
+    assert infidelity(want, got) <= 1e-6
+    assert np.max(np.abs(got - want)) <= 1e-5

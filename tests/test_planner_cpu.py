@@ -222,12 +222,13 @@ def test_fault_injection_on_host(monkeypatch):
     assert "injected" in str(e.value)
 
 
+@pytest.mark.parametrize("mode", [qs.QS_TC_BF16X3, qs.QS_TC_TF32X3])
 @pytest.mark.parametrize("n", [13, 15])
-def test_tensor_core_plans_match_oracle(n):
+def test_tensor_core_plans_match_oracle(n, mode):
     """Tensor-core mode fuses into <= 6-qubit dense blocks (4+ qubit blocks padded to 6 run as
     tensor-core steps); the listing carries the FP64 fused matrices, replayed on the oracle."""
     gates = W.layered(n, 4, 11) + W.random_circuit(n, 40, 12, ALL)
-    info, stats = check_plan(gates, n, qs.options(tc=qs.QS_TC_BF16X3, dtype=qs.QS_C64))
+    info, stats = check_plan(gates, n, qs.options(tc=mode, dtype=qs.QS_C64))
     assert info["tc_gates"] > 0
 
 
@@ -303,12 +304,16 @@ def test_factored_rotations_replay_against_oracle(dtype):
     text = qs.qs_plan_dump(plan)
     qs.qs_plan_destroy(plan)
     _, items, _ = PR.parse_dump(text)
-    unit = anti = 0
+    forms = {"N": 0, "NM": 0, "A": 0, "AM": 0}
     for it in items:
         if it[0] == "OP" and it[1] == "DENSE" and len(it[2]) == 1 and not it[3]:
             m = it[4]
-            unit += int(m[0, 0] == 1 and m[1, 1] == 1)
-            anti += int(m[0, 1] == 1 and m[1, 0] == 1)
-    assert unit > 0 and anti > 0
+            if m[0, 0] == 1:
+                forms["N" if m[1, 1] == 1 else "NM" if m[1, 1] == -1 else "N?"] = 1 + forms.get("N", 0)
+            elif m[0, 1] == 1:
+                forms["A" if m[1, 0] == 1 else "AM" if m[1, 0] == -1 else "A?"] = 1 + forms.get("A", 0)
+    # rotations give N / AM, reflections (H) NM, rotations with |cos| < |sin| A or AM
+    assert forms["N"] and forms["NM"] and (forms["A"] or forms["AM"]), forms
+    assert "N?" not in forms and "A?" not in forms
     check_plan(gates, n, qs.options(dtype=dtype))
     off, _ = check_plan(gates, n, qs.options(dtype=dtype, factor=1))
