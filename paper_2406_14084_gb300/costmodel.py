@@ -26,7 +26,8 @@ def max_slab_bits(dtype: int) -> int:
 
 
 def candidate_options(dtype: int, n: int):
-    """The learned planner's grid (Euler split x fusion width / forced fusion x slab bits x stage bits)."""
+    """The learned planner's grid (Euler split x fusion width / forced fusion x slab bits x stage
+    bits x stage-table condition bits)."""
     bmax = min(max_slab_bits(dtype), n)
     rbmax = 5 if dtype == qs.QS_C64 else 4
     out = []
@@ -34,7 +35,9 @@ def candidate_options(dtype: int, n: int):
         for fw, force in FUSES:
             for sb in range(max(bmax - 2, 6), bmax + 1):
                 for rb in (rbmax - 1, rbmax):
-                    out.append(dict(fuse_width=fw, fuse_force=force, slab_bits=sb, stage_bits=rb, euler=eu))
+                    for mb in (0, 8):
+                        out.append(dict(fuse_width=fw, fuse_force=force, slab_bits=sb, stage_bits=rb, euler=eu,
+                                        merge_bits=mb))
     return out
 
 
@@ -72,7 +75,8 @@ def collect(target_rows: int, seed: int, nmin: int, nmax: int, dtypes=(qs.QS_C64
             n = lo + rng.below(nmax - lo + 1)
             name, gates = random_circuit_family(rng, n)
             grid = candidate_options(dtype, n)
-            o = grid[rng.below(len(grid))]
+            # a quarter of the plans with the greedy planner's own options, the rest from the grid
+            o = {} if rng.below(4) == 0 else grid[rng.below(len(grid))]
             plan = qs.qs_fuse(gates, n, qs.options(dtype=dtype, **o))
             try:
                 feats = qs.qs_plan_features(plan)

@@ -36,7 +36,8 @@
 namespace qs {
 namespace {
 
-constexpr int kThreads = 256;  // 8 warps: two per TMEM lane quarter
+constexpr int kThreads = 512;  // 16 warps: four per TMEM lane quarter
+constexpr uint32_t kChunksPerThread = 16 * kTcRows / kThreads;  // 16-byte operand chunks of a row part
 // One operand part in shared memory: a BF16 operand (128 x 128 x 2 B), or half the K range of a
 // TF32 operand (128 x 64 x 4 B): 32 KiB either way.
 constexpr uint32_t kOpBytes = kTcRows * kTcK * 2;
@@ -285,12 +286,12 @@ __global__ void __launch_bounds__(kThreads, 1)
         const bool more = s + gridDim.x < nslabs;
         for (int h = 0; h < kParts; ++h) {
             if (kTf32) load_b(h);  // the B region is free: the previous GEMM has completed
-            // split row m into hi / lo in the swizzled operand layout, 16-byte chunks half*8 ..
-            // half*8+7 of the row's 16 (thread (m, half) = (tid % 128, tid / 128))
-            const uint32_t m = tid & 127u, mo = K.moff[m], c16b = (tid >> 7) * 8;
+            // split row m into hi / lo in the swizzled operand layout: thread (m, p) =
+            // (tid % 128, tid / 128) converts 16-byte chunks p*4 .. p*4+3 of the row's 16
+            const uint32_t m = tid & 127u, mo = K.moff[m], c16b = (tid >> 7) * kChunksPerThread;
             if (!kTf32) {
-#pragma unroll 2
-                for (uint32_t c16 = c16b; c16 < c16b + 8; ++c16) {
+#pragma unroll
+                for (uint32_t c16 = c16b; c16 < c16b + kChunksPerThread; ++c16) {
                     __nv_bfloat162 hv[4], lv[4];
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
@@ -306,8 +307,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
             } else {
                 // K half h holds targets j = 32h .. 32h + 31; a chunk is 2 amplitudes (re, im, re, im)
-#pragma unroll 2
-                for (uint32_t c16 = c16b; c16 < c16b + 8; ++c16) {
+#pragma unroll
+                for (uint32_t c16 = c16b; c16 < c16b + kChunksPerThread; ++c16) {
                     const uint32_t j = 32u * uint32_t(h) + 2u * c16;
                     const float2 a0 = slab[mo | K.joff[j]], a1 = slab[mo | K.joff[j + 1]];
                     const float xs[4] = {a0.x, a0.y, a1.x, a1.y};
@@ -362,11 +363,12 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         if (failed) break;
         // epilogue: warp w reads rows 32q..32q+31 of its TMEM lane quarter q = w % 4, columns
-        // 64h..64h+63 with h = w / 4, 32 columns at a time, into the free operand region
+        // 32h..32h+31 with h = w / 4, into the free operand region
         {
-            const uint32_t q4 = warp & 3u, m = q4 * 32 + lane, mo = K.moff[m], cb = (warp >> 2) * (kTcK / 2);
+            constexpr uint32_t kCols = kTcK / (kThreads / 128);
+            const uint32_t q4 = warp & 3u, m = q4 * 32 + lane, mo = K.moff[m], cb = (warp >> 2) * kCols;
 #pragma unroll 1
-            for (uint32_t c0 = cb; c0 < cb + kTcK / 2; c0 += 32) {
+            for (uint32_t c0 = cb; c0 < cb + kCols; c0 += 32) {
                 float r[32];
                 tmem_ld32(tmem + ((q4 * 32u) << 16) + c0, r);
 #pragma unroll

@@ -172,20 +172,23 @@ int learned_choose(const std::vector<CGate> &gates, int n, qs_dtype dt, const qs
     };
     const Fuse fuses[] = {{1, 0}, {2, 0}, {3, 1}, {4, 1}, {5, 1}};
     std::vector<qs_options> cand;
+    const int merges[] = {0, 8};  // stage-table condition bits: the default 6, or 8
     for (int eu = 1; eu <= 2; ++eu)
         for (const Fuse &fz : fuses)
             for (int sb = std::max(bmax - 2, 6); sb <= bmax; ++sb)
-                for (int rb = rbmax - 1; rb <= rbmax; ++rb) {
-                    qs_options o = opt;
-                    o.planner = QS_PLANNER_GREEDY;
-                    o.fuse_width = fz.width;
-                    o.fuse_force = fz.force;
-                    o.slab_bits = sb;
-                    o.stage_bits = rb;
-                    o.slab_mode = QS_SLAB_GATHER;
-                    o.euler = eu;
-                    cand.push_back(o);
-                }
+                for (int rb = rbmax - 1; rb <= rbmax; ++rb)
+                    for (int mb : merges) {
+                        qs_options o = opt;
+                        o.planner = QS_PLANNER_GREEDY;
+                        o.fuse_width = fz.width;
+                        o.fuse_force = fz.force;
+                        o.slab_bits = sb;
+                        o.stage_bits = rb;
+                        o.slab_mode = QS_SLAB_GATHER;
+                        o.euler = eu;
+                        o.merge_bits = mb;
+                        cand.push_back(o);
+                    }
     const size_t nc = cand.size();
     std::vector<Plan> plans(nc);
     std::vector<int> ok(nc, 0);
