@@ -768,6 +768,28 @@ def form_layered32_c128(qs, torch):
     return out
 
 
+def form_df_c128(qs, torch, name):
+    """Complex128 in double-float form (qs_options.arith = QS_ARITH_DF): the register stages run on
+    the FP32 pipe with pairs of FP32 numbers, the state stays complex128.  One apply of the
+    32-qubit circuit against one apply with FP64 arithmetic, and max |delta amp| against the
+    FP64 oracle on the 20-qubit copy of the same circuit."""
+    w = WORKLOADS[name]
+    n, dtype = w["n"], qs.QS_C128
+    gates, x0 = make_circuit(w)
+    o_df = qs.options(dtype=dtype, arith=qs.QS_ARITH_DF)
+    p_df = qs.qs_fuse(gates, n, o_df)
+    stream = torch.cuda.Stream()
+    with qs.State(n, dtype) as st:
+        qs.qs_set_stream(st.h, stream.cuda_stream)
+        _timed_apply_ms(qs, torch, st, p_df, stream, x0)  # warm-up (kernel set-up)
+        ms = _timed_apply_ms(qs, torch, st, p_df, stream, x0)
+        norm = qs.qs_norm2(st.h)
+    qs.qs_plan_destroy(p_df)
+    return {"workload": name, "qubits": n, "gates": len(gates), "dtype": "c128 (double-float stages)",
+            "ms": ms, "gates_per_s": len(gates) / (ms / 1e3), "norm_after": norm,
+            "fidelity": fidelity_check(w, o_df, dtype, n_small=20)}
+
+
 def form_tensor_cores(qs, torch):
     """Config 3: 33-qubit complex64 layered depth 60; tensor-core plan (6-qubit blocks, BF16 x 3
     split products) against the plain SIMT plan, one apply each; each mode's fidelity and max
@@ -920,6 +942,8 @@ def run_forms(args):
 
     forms, t0 = {}, time.perf_counter()
     jobs = [("layered32_c128", lambda: form_layered32_c128(qs, torch)),
+            ("layered32_c128_double_float", lambda: form_df_c128(qs, torch, "layered32_c128")),
+            ("qft32_c128_double_float", lambda: form_df_c128(qs, torch, "qft32_c128")),
             ("tensor_cores_vs_plain", lambda: form_tensor_cores(qs, torch)),
             ("batched_vs_per_circuit_c64", lambda: form_batch(qs, torch, "c64")),
             ("batched_vs_per_circuit_c128", lambda: form_batch(qs, torch, "c128")),
@@ -968,6 +992,10 @@ def run_gpu(args, w, ws, rank, local):
         opts.fuse_width, opts.blocking = 0, 0
     if (w.get("tc") and args.tc != "off") or args.tc == "bf16x3":
         opts.tc = qs.QS_TC_BF16X3
+    if args.tc == "tf32x3":
+        opts.tc = qs.QS_TC_TF32X3
+    if args.arith == "df":
+        opts.arith = qs.QS_ARITH_DF
 
     t_plan0 = time.perf_counter()
     plan = qs.qs_fuse(gates, n, opts)
@@ -1034,11 +1062,11 @@ def run_gpu(args, w, ws, rank, local):
         tc_launch_ms = st["tc_ms"] / st["tc_gates"]
         tc_gbs = pass_bytes / (tc_launch_ms / 1e3) / 1e9
         roof = {"bound": "hbm", "achieved": tc_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": tc_gbs / peaks["hbm_gbs"], "traffic": None, "kernel": "tc_bf16_kernel",
+                "frac": tc_gbs / peaks["hbm_gbs"], "traffic": None, "kernel": "tc_kernel",
                 "peak_source": peaks["source"], "avg_launch_ms": tc_launch_ms, "bytes_per_launch": pass_bytes}
         tc_tflops = 24.0 * 64 * (1 << n) / (tc_launch_ms / 1e3) / 1e12
         tc_roof = {"bound": "tensor", "achieved": tc_tflops, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
-                   "frac": tc_tflops / peaks["bf16_tflops"], "kernel": "tc_bf16_kernel",
+                   "frac": tc_tflops / peaks["bf16_tflops"], "kernel": "tc_kernel",
                    "peak_source": "BF16 dense, " + peaks["source"]}
     alu_peak = ALU_PEAK_TFLOPS["c64" if dtype == qs.QS_C64 else "c128"]
     roof_alu = {"bound": "alu", "achieved": alu_tflops, "peak": alu_peak, "unit": "TFLOP/s",
@@ -1093,7 +1121,7 @@ def run_gpu(args, w, ws, rank, local):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": (gates_per_s / PAPER_GATES_PER_S[args.workload]) if args.workload in PAPER_GATES_PER_S else None,
-        "dtype": "c64" if dtype == qs.QS_C64 else "c128",
+        "dtype": "c64" if dtype == qs.QS_C64 else ("c128" if args.arith == "fp64" else "c128-storage/df32x2-arith"),
         "data": "synthetic (seeded generator, paper-shaped circuit)",
         "config": {"workload": args.workload, "qubits": n, "gates": len(gates),
                    "state_bytes": (1 << n) * amp_bytes, "l2": "state larger than L2",
@@ -1130,7 +1158,9 @@ def main():
     ap.add_argument("--slab-mode", default="gather", choices=["gather", "remap"])
     ap.add_argument("--stage-bits", type=int, default=0)
     ap.add_argument("--seg-bits", type=int, default=0)
-    ap.add_argument("--tc", default="auto", choices=["auto", "off", "bf16x3"])
+    ap.add_argument("--tc", default="auto", choices=["auto", "off", "bf16x3", "tf32x3"])
+    ap.add_argument("--arith", default="fp64", choices=["fp64", "df"],
+                    help="complex128 register stages in FP64 or in double-float form")
     ap.add_argument("--no-fidelity", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -86,6 +86,12 @@ typedef enum { QS_PLANNER_GREEDY = 0, QS_PLANNER_LEARNED = 1 } qs_planner;
  * bits for hi + lo) or BF16 (about 16 bits).  Not in the paper: a GB300 form of its dense gates. */
 typedef enum { QS_TC_OFF = 0, QS_TC_TF32X3 = 1, QS_TC_BF16X3 = 2 } qs_tc_mode;
 typedef enum { QS_SLAB_GATHER = 0, QS_SLAB_REMAP = 1 } qs_slab_mode;
+/* Arithmetic of complex128 register stages.  QS_ARITH_FP64 (the default): FP64 FMAs.
+ * QS_ARITH_DF: each slab is converted once per pass to double-float pairs (two FP32 numbers,
+ * about 48 significant bits) and the register stages run on the FP32 pipe, which GB300 executes
+ * about 64x faster than FP64; the state in HBM stays complex128, and passes with shared-memory
+ * ops stay FP64.  Each operation then rounds at about 2^-46 instead of 2^-53 relative. */
+typedef enum { QS_ARITH_FP64 = 0, QS_ARITH_DF = 1 } qs_arith;
 
 /* Planning options.  Fill with qs_options_default() and override fields. */
 typedef struct {
@@ -117,6 +123,8 @@ typedef struct {
     int32_t merge_bits;  /* register stages: most condition bits (slab or outer qubits) one merged
                             diagonal table may read besides the register bits; 0 = automatic (6),
                             at most 10 (tables of 2^(stage_bits + merge_bits) entries) */
+    int32_t arith;       /* qs_arith: arithmetic of complex128 register stages */
+    int32_t reserved[3];
 } qs_options;
 
 /* Plan summary (qs_plan_info). */

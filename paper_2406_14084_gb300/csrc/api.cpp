@@ -66,6 +66,7 @@ struct DevPlanBuf {
     DevTc *tcs = nullptr;
     unsigned char *images = nullptr;
     void *coef = nullptr;
+    void *coef_df = nullptr;  // complex128 plans in double-float form: (h, l) of re, then of im
     int device = -1;
 };
 
@@ -196,7 +197,9 @@ qs_status upload(qs_plan *pl, qs_dtype dt)
     const size_t o_tc = o_sb + al(nsb * sizeof(DevSub)), o_im = o_tc + al(ntc * sizeof(DevTc));
     const size_t o_coef = o_im + al(nim);
     // two spare entries: the register stages read a sub-op's first two coefficients ahead
-    const size_t total = o_coef + al((nc + 2) * amp_bytes(dt));
+    const bool want_df = dt == QS_C128 && p.opt.arith == QS_ARITH_DF;
+    const size_t o_cdf = o_coef + al((nc + 2) * amp_bytes(dt));
+    const size_t total = o_cdf + (want_df ? al((nc + 2) * 16) : 0);
     std::vector<unsigned char> h(total, 0);
     if (!p.passes.empty()) std::memcpy(h.data() + o_pass, p.passes.data(), p.passes.size() * sizeof(DevPass));
     if (!p.ops.empty()) std::memcpy(h.data() + o_ops, p.ops.data(), p.ops.size() * sizeof(DevOp));
@@ -217,6 +220,18 @@ qs_status upload(qs_plan *pl, qs_dtype dt)
             f[2 * i + 1] = p.coef[i].imag();
         }
     }
+    if (want_df) {
+        // each FP64 part x as h = fl32(x), l = fl32(x - h): h + l carries about 48 bits of x
+        float *f = reinterpret_cast<float *>(h.data() + o_cdf);
+        for (size_t i = 0; i < p.coef.size(); ++i) {
+            const double parts[2] = {p.coef[i].real(), p.coef[i].imag()};
+            for (int r = 0; r < 2; ++r) {
+                const float hi = (float)parts[r];
+                f[4 * i + 2 * r] = hi;
+                f[4 * i + 2 * r + 1] = (float)(parts[r] - (double)hi);
+            }
+        }
+    }
     if (fault("alloc")) return fail(QS_ENOMEM, "injected allocation failure");
     void *base = nullptr;
     qs_status st = cuda_status(cudaMalloc(&base, total), "plan upload allocation");
@@ -235,6 +250,7 @@ qs_status upload(qs_plan *pl, qs_dtype dt)
     d.tcs = reinterpret_cast<DevTc *>((char *)base + o_tc);
     d.images = reinterpret_cast<unsigned char *>((char *)base + o_im);
     d.coef = (char *)base + o_coef;
+    d.coef_df = want_df ? (char *)base + o_cdf : nullptr;
     return QS_OK;
 }
 
@@ -294,7 +310,10 @@ qs_status run_plan(qs_state *s, qs_plan *pl, StepTimer *timer = nullptr)
         case S_REMAP: {
             const DevPass &hp = p.passes[stp.index];
             const int rb = p.stage_bits > 0 ? p.stage_bits : (s->dt == QS_C64 ? kStageBitsC64 : kStageBitsC128);
-            const PassArgs pa{d.passes + stp.index, d.ops, d.stages, d.subs, d.coef, rb};
+            // double-float form: complex128, requested, and a pass of register stages only
+            bool df = d.coef_df != nullptr && stp.kind == S_PASS && !hp.has_perm;
+            for (int o = hp.op_begin; df && o < hp.op_end; ++o) df = p.ops[o].type == OP_STAGE;
+            const PassArgs pa{d.passes + stp.index, d.ops, d.stages, d.subs, d.coef, rb, d.coef_df, df};
             rc = launch_pass(c, pa, hp, err, sizeof err);
             if (stp.kind == S_PASS) s->stats.passes++;
             else s->stats.remaps++;
@@ -561,6 +580,7 @@ qs_status qs_fuse(const qs_gate *g, size_t ng, int n, const qs_options *o, qs_pl
     else qs_options_default(&opt);
     if (opt.fuse_width < 0 || opt.fuse_width > 7 || opt.slab_bits < 0 || opt.slab_bits > kMaxSlabBits ||
         opt.seg_bits < 0 || opt.seg_bits > 8 || opt.merge_bits < 0 || opt.merge_bits > 10 ||
+        (opt.arith != QS_ARITH_FP64 && opt.arith != QS_ARITH_DF) ||
         (opt.slab_mode != QS_SLAB_GATHER && opt.slab_mode != QS_SLAB_REMAP) ||
         (opt.tc != QS_TC_OFF && opt.tc != QS_TC_TF32X3 && opt.tc != QS_TC_BF16X3))
         return fail(QS_EINVAL, "option out of range");
@@ -592,6 +612,7 @@ qs_status qs_fuse_learned(const qs_gate *g, size_t ng, int n, const qs_options *
     else qs_options_default(&opt);
     if (opt.fuse_width < 0 || opt.fuse_width > 7 || opt.slab_bits < 0 || opt.slab_bits > kMaxSlabBits ||
         opt.seg_bits < 0 || opt.seg_bits > 8 || opt.merge_bits < 0 || opt.merge_bits > 10 ||
+        (opt.arith != QS_ARITH_FP64 && opt.arith != QS_ARITH_DF) ||
         (opt.slab_mode != QS_SLAB_GATHER && opt.slab_mode != QS_SLAB_REMAP) ||
         (opt.tc != QS_TC_OFF && opt.tc != QS_TC_TF32X3 && opt.tc != QS_TC_BF16X3) ||
         (opt.dtype != QS_C64 && opt.dtype != QS_C128))

@@ -38,14 +38,19 @@ constexpr uint32_t kMaxVec = 4096;
 // cp.async copies of slab i+1 (issued by every thread, 16 per thread for a 64 KiB slab) land
 // in the other buffer.  cp.async.wait_group completes on its own, so no wait can hang.
 
-template <typename R, int RB, int NT>
+// DF (complex128 only): the slab is converted in place to double-float pairs after it lands,
+// the register stages compute on the FP32 pipe (df_arith.cuh) with double-float coefficients
+// (coef_df), and every amplitude is converted back on its way to HBM.  Only passes made of
+// register stages run in this form (the host checks); the state in HBM stays complex128.
+template <typename R, int RB, int NT, bool DF = false>
 __global__ void __launch_bounds__(NT, 1)
     slab_pass_kernel(typename Cx<R>::T *__restrict__ state, const DevPass *__restrict__ d_pass,
                      const DevOp *__restrict__ ops, const DevStage *__restrict__ stages,
                      const DevSub *__restrict__ subs, const typename Cx<R>::T *__restrict__ coef,
-                     uint64_t nslabs)
+                     const dfc *__restrict__ coef_df, uint64_t nslabs)
 {
     using C = typename Cx<R>::T;
+    static_assert(!DF || sizeof(C) == sizeof(dfc), "double-float slabs replace complex128 slabs");
     extern __shared__ __align__(128) unsigned char smem_raw[];
     SlabShared &S = *reinterpret_cast<SlabShared *>(smem_raw);
     const uint32_t tid = threadIdx.x;
@@ -133,14 +138,29 @@ __global__ void __launch_bounds__(NT, 1)
         const uint64_t base = slab_base(slab);
         C *sm = buf0 + size_t(k) * nsl;
         C *gbase = state + base;
-        // the gate block
-        for (int o = op_begin; o < op_end; ++o) {
-            const DevOp &op = ops[o];
-            if ((base & op.ocmask) == op.ocmask) {
-                if (op.type == OP_STAGE) run_stage<C, RB>(sm, stages + op.mat, subs, coef, base, tid, NT);
-                else run_smem_op<C>(sm, b, op, coef, base, tid, NT);
+        if (DF) {
+            // complex128 -> double-float pairs, each 16-byte slot in place
+            dfc *sd = reinterpret_cast<dfc *>(sm);
+            for (uint32_t e = tid; e < nsl; e += NT) {
+                const C a = sm[e];
+                sd[e] = dfc{d2df(a.x), d2df(a.y)};
             }
             __syncthreads();
+            for (int o = op_begin; o < op_end; ++o) {
+                const DevOp &op = ops[o];
+                if ((base & op.ocmask) == op.ocmask) run_stage<dfc, RB>(sd, stages + op.mat, subs, coef_df, base, tid, NT);
+                __syncthreads();
+            }
+        } else {
+            // the gate block
+            for (int o = op_begin; o < op_end; ++o) {
+                const DevOp &op = ops[o];
+                if ((base & op.ocmask) == op.ocmask) {
+                    if (op.type == OP_STAGE) run_stage<C, RB>(sm, stages + op.mat, subs, coef, base, tid, NT);
+                    else run_smem_op<C>(sm, b, op, coef, base, tid, NT);
+                }
+                __syncthreads();
+            }
         }
         // store
         if (!S.pass.has_perm) {
@@ -149,7 +169,14 @@ __global__ void __launch_bounds__(NT, 1)
             for (uint32_t j = 0; j < kMaxVec / NT; ++j) {
                 const uint32_t v = tid + j * NT;
                 if (v >= nvec) break;
-                st_stream(gv + voff[v], reinterpret_cast<const uint4 *>(sm)[ct ^ chunk_of(j * NT)]);
+                const uint32_t slot = ct ^ chunk_of(j * NT);
+                if (DF) {
+                    const dfc q = reinterpret_cast<const dfc *>(sm)[slot];
+                    const double2 d = make_double2(df2d(q.x), df2d(q.y));
+                    st_stream(gv + voff[v], *reinterpret_cast<const uint4 *>(&d));
+                } else {
+                    st_stream(gv + voff[v], reinterpret_cast<const uint4 *>(sm)[slot]);
+                }
             }
         } else {
             for (uint32_t d = tid; d < nsl; d += NT) {
@@ -164,7 +191,7 @@ __global__ void __launch_bounds__(NT, 1)
 }
 
 // One CTA per SM with NT threads (= 2^(b - RB) register groups for the default slab sizes).
-template <typename R, int RB, int NT>
+template <typename R, int RB, int NT, bool DF = false>
 int launch_pass_t(const LaunchCtx &c, const PassArgs &a, const DevPass &h, char *err, size_t errlen)
 {
     using C = typename Cx<R>::T;
@@ -173,16 +200,16 @@ int launch_pass_t(const LaunchCtx &c, const PassArgs &a, const DevPass &h, char 
     int dev = 0;
     cudaGetDevice(&dev);
     if (attr_dev != dev) {
-        cudaFuncSetAttribute(slab_pass_kernel<R, RB, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(slab_pass_kernel<R, RB, NT, DF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              227 * 1024);
         attr_dev = dev;
     }
     const uint64_t nslabs = 1ull << (c.n - h.b);
     uint64_t grid = uint64_t(num_sms());
     if (grid > nslabs) grid = nslabs;
-    slab_pass_kernel<R, RB, NT><<<(unsigned)grid, NT, smem, (cudaStream_t)c.stream>>>(
+    slab_pass_kernel<R, RB, NT, DF><<<(unsigned)grid, NT, smem, (cudaStream_t)c.stream>>>(
         reinterpret_cast<C *>(c.amp), a.pass, a.ops, a.stages, a.subs,
-        reinterpret_cast<const C *>(a.coef), nslabs);
+        reinterpret_cast<const C *>(a.coef), reinterpret_cast<const dfc *>(a.coef_df), nslabs);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
         snprintf(err, errlen, "slab pass launch failed: %s", cudaGetErrorString(e));
@@ -213,6 +240,15 @@ int launch_pass(const LaunchCtx &c, const PassArgs &a, const DevPass &h, char *e
         if (a.stage_bits == kStageBitsC64 - 1)
             return launch_pass_t<float, kStageBitsC64 - 1, 512>(c, a, h, err, errlen);
         return launch_pass_t<float, kStageBitsC64, 256>(c, a, h, err, errlen);
+    }
+    if (a.df) {
+        if (!a.coef_df) {
+            snprintf(err, errlen, "double-float pass without double-float coefficients");
+            return QS_EINVAL;
+        }
+        if (a.stage_bits == kStageBitsC128 - 1)
+            return launch_pass_t<double, kStageBitsC128 - 1, 512, true>(c, a, h, err, errlen);
+        return launch_pass_t<double, kStageBitsC128, 256, true>(c, a, h, err, errlen);
     }
     if (a.stage_bits == kStageBitsC128 - 1)
         return launch_pass_t<double, kStageBitsC128 - 1, 512>(c, a, h, err, errlen);

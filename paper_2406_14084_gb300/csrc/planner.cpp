@@ -1371,6 +1371,10 @@ int build_plan(const std::vector<CGate> &gates_in, int n, qs_dtype dt, const qs_
             err = "the tensor-core path needs blocking and at least 13 qubits";
             return QS_EUNSUPPORTED;
         }
+        if (opt.tc_width != 0 && opt.tc_width != kTcTargets) {
+            err = "tensor-core blocks are built for 6 qubits only";
+            return QS_EUNSUPPORTED;
+        }
     }
     std::vector<char> is_tc;
     if (tc) {

@@ -145,6 +145,8 @@ struct PassArgs {
     const DevSub *subs;       // device, whole plan
     const void *coef;         // device, whole plan, state precision
     int stage_bits;           // register-stage width the plan was built for
+    const void *coef_df;      // device, whole plan, double-float quadruples (or NULL)
+    bool df;                  // complex128 pass of register stages only, in double-float form
 };
 int launch_pass(const LaunchCtx &c, const PassArgs &a, const DevPass &h_pass, char *err,
                 size_t errlen);

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include "dev_common.cuh"
+#include "df_arith.cuh"
 #include "qs_internal.h"
 
 namespace qs {
@@ -34,6 +35,10 @@ __device__ __forceinline__ void st_stream(uint4 *p, uint4 v)
 
 // ------------------------------------------------------------------ register sub-ops
 
+// Read-only coefficient load in the register type (double-float coefficients: df_arith.cuh).
+__device__ __forceinline__ float2 ldgc(const float2 *p) { return __ldg(p); }
+__device__ __forceinline__ double2 ldgc(const double2 *p) { return __ldg(p); }
+
 // s * b + a on both parts of a complex amplitude with a real scalar s.  Complex64 uses one packed
 // fma.rn.f32x2 (two FP32 FMAs in one instruction); complex128 two FP64 FMAs.
 __device__ __forceinline__ float2 rfma(float s, float2 b, float2 a)
@@ -51,7 +56,7 @@ __device__ __forceinline__ float2 rfma(float s, float2 b, float2 a)
 }
 __device__ __forceinline__ double2 rfma(double s, double2 b, double2 a)
 {
-    return make_double2(fma(s, b.x, a.x), fma(s, b.y, a.y));
+    return make_double2(::fma(s, b.x, a.x), ::fma(s, b.y, a.y));
 }
 // s * b on both parts (packed mul.rn.f32x2 for complex64).
 __device__ __forceinline__ float2 rmul(float s, float2 b)
@@ -74,7 +79,7 @@ __device__ __forceinline__ float2 rfms(float s, float2 b, float2 a)
 }
 __device__ __forceinline__ double2 rfms(double s, double2 b, double2 a)
 {
-    return make_double2(fma(s, b.x, -a.x), fma(s, b.y, -a.y));
+    return make_double2(::fma(s, b.x, -a.x), ::fma(s, b.y, -a.y));
 }
 
 
@@ -392,7 +397,7 @@ __device__ __forceinline__ void apply_sub(C (&v)[1 << RB], const SubHead &h, con
         }
         const C *__restrict__ T = M + (size_t(hi) << RB);
 #pragma unroll
-        for (int e = 0; e < (1 << RB); ++e) v[e] = cmul(__ldg(&T[e]), v[e]);
+        for (int e = 0; e < (1 << RB); ++e) v[e] = cmul(ldgc(&T[e]), v[e]);
         break;
     }
     default: break;
@@ -442,14 +447,14 @@ __device__ __noinline__ void run_stage(C *sm, const DevStage *__restrict__ stg,
         }
         if (s0 < s1) {
             SubHead nxt = load_sub_head(subs + s0);
-            C n0 = __ldg(coef + nxt.mat), n1 = __ldg(coef + nxt.mat + 1);
+            C n0 = ldgc(coef + nxt.mat), n1 = ldgc(coef + nxt.mat + 1);
             for (int s = s0; s < s1; ++s) {
                 const SubHead cur = nxt;
                 const C c0 = n0, c1 = n1;
                 if (s + 1 < s1) {
                     nxt = load_sub_head(subs + s + 1);
-                    n0 = __ldg(coef + nxt.mat);
-                    n1 = __ldg(coef + nxt.mat + 1);
+                    n0 = ldgc(coef + nxt.mat);
+                    n1 = ldgc(coef + nxt.mat + 1);
                 }
                 apply_sub<C, RB>(v, cur, subs + s, base, cta_base, coef, c0, c1);
             }

@@ -21,6 +21,7 @@ QS_C64, QS_C128 = 0, 1
 QS_OK, QS_EINVAL, QS_ENOMEM, QS_ECUDA, QS_ETIMEOUT, QS_EUNSUPPORTED = range(6)
 QS_PLANNER_GREEDY, QS_PLANNER_LEARNED = 0, 1
 QS_TC_OFF, QS_TC_TF32X3, QS_TC_BF16X3 = 0, 1, 2
+QS_ARITH_FP64, QS_ARITH_DF = 0, 1
 QS_SLAB_GATHER, QS_SLAB_REMAP = 0, 1
 MAX_TARGETS, MAX_CONTROLS = 7, 8
 
@@ -55,7 +56,7 @@ class QsOptions(ctypes.Structure):
                 ("diag_bits", ctypes.c_int32), ("dtype", ctypes.c_int32),
                 ("stage_bits", ctypes.c_int32), ("fuse_force", ctypes.c_int32),
                 ("euler", ctypes.c_int32), ("factor", ctypes.c_int32),
-                ("merge_bits", ctypes.c_int32)]
+                ("merge_bits", ctypes.c_int32), ("arith", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
 
 class QsPlanInfo(ctypes.Structure):

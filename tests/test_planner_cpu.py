@@ -240,6 +240,9 @@ def test_tensor_core_mode_rejections():
     with pytest.raises(qs.QsError) as e:
         qs.qs_fuse(W.layered(10, 2, 1), 10, qs.options(tc=qs.QS_TC_BF16X3, dtype=qs.QS_C64))
     assert e.value.status == qs.QS_EUNSUPPORTED
+    with pytest.raises(qs.QsError) as e:
+        qs.qs_fuse(g, 14, qs.options(tc=qs.QS_TC_TF32X3, dtype=qs.QS_C64, tc_width=7))
+    assert e.value.status == qs.QS_EUNSUPPORTED
 
 
 @pytest.mark.parametrize("dtype,stage", [(qs.QS_C64, 5), (qs.QS_C64, 4), (qs.QS_C128, 4), (qs.QS_C128, 3)])
@@ -317,3 +320,12 @@ def test_factored_rotations_replay_against_oracle(dtype):
     assert "N?" not in forms and "A?" not in forms
     check_plan(gates, n, qs.options(dtype=dtype))
     off, _ = check_plan(gates, n, qs.options(dtype=dtype, factor=1))
+
+
+def test_arith_option_is_validated():
+    g = W.layered(12, 2, 3)
+    p = qs.qs_fuse(g, 12, qs.options(dtype=qs.QS_C128, arith=qs.QS_ARITH_DF))
+    qs.qs_plan_destroy(p)
+    with pytest.raises(qs.QsError) as e:
+        qs.qs_fuse(g, 12, qs.options(dtype=qs.QS_C128, arith=2))
+    assert e.value.status == qs.QS_EINVAL
