@@ -88,7 +88,7 @@ PAPER_GATES_PER_S = {"qaoa31_c128": 2511 / 17.5, "qft31_c128": 496 / 3.6}
 # per SM per clock (128 FP32, 2 FP64) x 2 flops per FMA.
 ALU_PEAK_TFLOPS = {"c64": 152 * 2.07e9 * 128 * 2 / 1e12, "c128": 152 * 2.07e9 * 2 * 2 / 1e12}
 
-TRAFFIC_SOURCES = ("k_slab.cu", "slab_common.cuh", "dev_common.cuh", "qs_internal.h")
+TRAFFIC_SOURCES = ("k_slab.cu", "slab_common.cuh", "dev_common.cuh", "df_arith.cuh", "qs_internal.h")
 
 
 def slab_kernel_hash() -> str:
@@ -817,7 +817,9 @@ def form_tensor_cores(qs, torch):
                 continue
             info = qs.qs_plan_info_get(p)
             qs.qs_stats_reset(st.h)
+            qs.qs_set_profiling(st.h, True)
             ms = _timed_apply_ms(qs, torch, st, p, stream, x0)
+            qs.qs_set_profiling(st.h, False)
             stt = qs.qs_stats(st.h)
             qs.qs_plan_destroy(p)
             r = {"ms": ms, "gates_per_s": len(gates) / (ms / 1e3), "speedup_vs_plain": ms_plain / ms,
@@ -942,12 +944,12 @@ def run_forms(args):
 
     forms, t0 = {}, time.perf_counter()
     jobs = [("layered32_c128", lambda: form_layered32_c128(qs, torch)),
-            ("layered32_c128_double_float", lambda: form_df_c128(qs, torch, "layered32_c128")),
-            ("qft32_c128_double_float", lambda: form_df_c128(qs, torch, "qft32_c128")),
             ("tensor_cores_vs_plain", lambda: form_tensor_cores(qs, torch)),
             ("batched_vs_per_circuit_c64", lambda: form_batch(qs, torch, "c64")),
-            ("batched_vs_per_circuit_c128", lambda: form_batch(qs, torch, "c128")),
-            ("learned_vs_greedy", lambda: form_learned(qs, torch, args.learned_n))]
+            ("learned_vs_greedy", lambda: form_learned(qs, torch, args.learned_n)),
+            ("layered32_c128_double_float", lambda: form_df_c128(qs, torch, "layered32_c128")),
+            ("qft32_c128_double_float", lambda: form_df_c128(qs, torch, "qft32_c128")),
+            ("batched_vs_per_circuit_c128", lambda: form_batch(qs, torch, "c128"))]
     for name, job in jobs:
         if time.perf_counter() - t0 > args.forms_budget:
             forms[name] = {"skipped": f"forms time budget of {args.forms_budget:.0f} s spent"}
@@ -1166,7 +1168,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--forms", default="auto", choices=["auto", "on", "off"])
-    ap.add_argument("--forms-budget", type=float, default=600.0)
+    ap.add_argument("--forms-budget", type=float, default=720.0)
     ap.add_argument("--learned-n", type=int, default=30)
     args = ap.parse_args()
     ws, rank, local = dist_env()

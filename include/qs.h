@@ -347,7 +347,7 @@ qs_status qs_batch_destroy(qs_batch *b);
  * fusion, slab bits, register-stage width), scores every step of every candidate in one
  * batched forward launch, and keeps the candidate with the lowest predicted total.  The greedy
  * plan (the caller's options as given) is the fallback -- it is kept when no candidate is
- * predicted faster by more than 5% -- and the judge: a learned plan carries its greedy twin,
+ * predicted faster by more than 2% -- and the judge: a learned plan carries its greedy twin,
  * the first qs_apply_plan times the learned plan, the second times the greedy plan, and every
  * later apply uses whichever was faster.  Both compute the same circuit.
  *

@@ -241,7 +241,9 @@ int learned_choose(const std::vector<CGate> &gates, int n, qs_dtype dt, const qs
     for (size_t k = 1; k < total.size(); ++k)
         if (total[k] < total[arg]) arg = k;
     meta.predicted_ms = total[0];
-    if (arg != 0 && total[arg] < 0.95 * total[0]) {
+    // the judge (two timed applies) protects against a wrong pick, so a 2 % predicted margin
+    // suffices
+    if (arg != 0 && total[arg] < 0.98 * total[0]) {
         meta.chosen = cidx[arg];
         meta.predicted_ms = total[arg];
         best = std::move(plans[cidx[arg]]);
