@@ -427,7 +427,19 @@ std::vector<CGate> fuse_pass(const std::vector<CGate> &in, int kdiag, int kdense
             }
             if (all_blocked) break;
         }
-        out.push_back(std::move(cur));
+        // a fused product that came out as the identity (H then H, RZ then RZ^-1, ...) does
+        // nothing: drop it (a uniform phase is kept, it is not the identity)
+        bool identity = cur.cls == C_DENSE || cur.cls == C_DIAG;
+        if (identity) {
+            const size_t D = size_t(1) << cur.tq.size();
+            for (size_t r = 0; identity && r < D; ++r)
+                for (size_t c = 0; identity && c < (cur.cls == C_DENSE ? D : 1); ++c) {
+                    const cd want = (cur.cls == C_DIAG || r == c) ? cd(1.0) : cd(0.0);
+                    const cd got = cur.cls == C_DIAG ? cur.m[r] : cur.m[r * D + c];
+                    identity = std::abs(got - want) <= 1e-14;
+                }
+        }
+        if (!identity) out.push_back(std::move(cur));
     }
     return out;
 }

@@ -329,3 +329,14 @@ def test_arith_option_is_validated():
     with pytest.raises(qs.QsError) as e:
         qs.qs_fuse(g, 12, qs.options(dtype=qs.QS_C128, arith=2))
     assert e.value.status == qs.QS_EINVAL
+
+
+def test_identity_products_are_dropped():
+    """H H and RZ(t) RZ(-t) fuse to the identity and leave no op; a uniform phase stays."""
+    n = 6
+    gates = [Gate("H", (2,)), Gate("H", (2,)), Gate("RZ", (4,), (), (0.7,)), Gate("RZ", (4,), (), (-0.7,))]
+    info, stats = check_plan(gates, n, qs.options(dtype=qs.QS_C128))
+    assert stats["ops"] == 0
+    phase = [Gate("DIAG", (1,), (), (), np.array([1j, 1j]))]
+    info, stats = check_plan(phase, n, qs.options(dtype=qs.QS_C128))
+    assert stats["ops"] == 1
