@@ -35,7 +35,7 @@ def candidate_options(dtype: int, n: int):
         for fw, force in FUSES:
             for sb in range(max(bmax - 2, 6), bmax + 1):
                 for rb in (rbmax - 1, rbmax):
-                    for mb in (0, 8):
+                    for mb in (0, 8, 10):
                         out.append(dict(fuse_width=fw, fuse_force=force, slab_bits=sb, stage_bits=rb, euler=eu,
                                         merge_bits=mb))
     return out
@@ -144,9 +144,14 @@ def main(argv=None):
     ap.add_argument("--epochs", type=int, default=60)
     ap.add_argument("--out", required=True, help=".npz for the trained model")
     ap.add_argument("--data", default=None, help="also save the timing data (.npz)")
+    ap.add_argument("--extra-data", default=None, help="earlier timing data (.npz) to train on too")
     a = ap.parse_args(argv)
     t0 = time.perf_counter()
     X, y, meta = collect(a.rows, a.seed, a.nmin, a.nmax, time_budget_s=a.budget)
+    if a.extra_data:
+        z = np.load(a.extra_data)
+        X = np.concatenate([X, z["X"].astype(np.float32)])
+        y = np.concatenate([y, z["y"].astype(np.float32)])
     t1 = time.perf_counter()
     if a.data:
         np.savez(a.data, X=X, y=y)
