@@ -791,14 +791,16 @@ def form_df_c128(qs, torch, name):
 
 
 def form_tensor_cores(qs, torch):
-    """Config 3: 33-qubit complex64 layered depth 60; tensor-core plan (6-qubit blocks, BF16 x 3
-    split products) against the plain SIMT plan, one apply each; each mode's fidelity and max
-    |delta amp| against the FP64 path on the 26-qubit copy, and against the oracle at 20 qubits."""
+    """Config 3: 33-qubit complex64 layered depth 60; tensor-core plans (6- and 7-qubit blocks,
+    BF16 x 3 and TF32 x 3 split products) against the plain SIMT plan, one apply each; each
+    mode's fidelity and max |delta amp| against the FP64 path on the 26-qubit copy, and against
+    the oracle at 20 qubits."""
     w = WORKLOADS["precision33_c64"]
     n, dtype = w["n"], qs.QS_C64
     gates, x0 = make_circuit(w)
     o_plain = qs.options(dtype=dtype)
-    modes = {"bf16x3": qs.QS_TC_BF16X3, "tf32x3": qs.QS_TC_TF32X3}
+    modes = {"bf16x3": (qs.QS_TC_BF16X3, 6), "tf32x3": (qs.QS_TC_TF32X3, 6),
+             "bf16x3_7q": (qs.QS_TC_BF16X3, 7), "tf32x3_7q": (qs.QS_TC_TF32X3, 7)}
     res = {"workload": "precision33_c64", "qubits": n, "gates": len(gates), "dtype": "c64", "modes": {}}
     stream = torch.cuda.Stream()
     p_plain = qs.qs_fuse(gates, n, o_plain)
@@ -808,8 +810,8 @@ def form_tensor_cores(qs, torch):
         res["plain"] = {"ms": ms_plain, "gates_per_s": len(gates) / (ms_plain / 1e3),
                         "passes": qs.qs_plan_info_get(p_plain)["passes"]}
         qs.qs_plan_destroy(p_plain)
-        for name, mode in modes.items():
-            o = qs.options(dtype=dtype, tc=mode)
+        for name, (mode, width) in modes.items():
+            o = qs.options(dtype=dtype, tc=mode, tc_width=width)
             try:
                 p = qs.qs_fuse(gates, n, o)
             except qs.QsError as e:

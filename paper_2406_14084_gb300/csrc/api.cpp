@@ -729,11 +729,11 @@ qs_status qs_plan_dump(const qs_plan *pl, char *buf, size_t cap, size_t *needed)
             num(T.slab.lo);
             for (int j = 0; j < T.slab.nhi; ++j) num(T.slab.hipos[j]);
             out += "\nOP DENSE";
-            num(kTcTargets);
+            num(T.width);
             out += " t";
             for (int q : p.tc_phys[s.index]) num(q);
             out += " c m";
-            for (size_t e = 0; e < (size_t(1) << (2 * kTcTargets)); ++e) cnum(p.coef[p.tc_coef[s.index] + e]);
+            for (size_t e = 0; e < (size_t(1) << (2 * T.width)); ++e) cnum(p.coef[p.tc_coef[s.index] + e]);
             out += "\n";
         } else if (s.kind == S_UNBLOCKED) {
             out += "UNBLOCKED\n";

@@ -47,7 +47,8 @@ constexpr uint32_t kOffAhi = kSlabBytes, kOffAlo = kOffAhi + kOpBytes, kOffBhi =
 constexpr uint32_t kWaitLimit = 1u << 24;
 
 struct TcCtl {
-    unsigned long long mbar;
+    unsigned long long mbar;  // MMA completion
+    unsigned long long bbar;  // E-image bulk copies landed
     uint32_t tmem;
     uint32_t pad;
     DevTc tc;
@@ -93,6 +94,21 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity)
         if (i > 64) __nanosleep(64);
     }
     return false;
+}
+
+// One thread: expect `bytes` of bulk copies on the mbarrier (one arrival).
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+// Bulk (TMA, non-tensor) copy global -> shared of `bytes` (16-byte aligned, multiple of 16),
+// completing on the mbarrier.
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
 }
 
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
@@ -179,11 +195,13 @@ __device__ __forceinline__ uint32_t op_chunk_offset(uint32_t row, uint32_t chunk
     return kb * (kTcRows * 128u) + row * 128u + ((c ^ (row & 7u)) << 4);
 }
 
-// MODE = QS_TC_BF16X3: E_hi / E_lo stay in shared memory for the whole launch and each slab is
-// one GEMM over K = 128.  MODE = QS_TC_TF32X3: the operands are 4-byte TF32, so a slab is two
-// GEMM halves over K = 64 each, and the E half-images are loaded from global memory (L2) for
-// every half.
-template <int MODE>
+// MODE = QS_TC_BF16X3: each GEMM is over K = 128.  MODE = QS_TC_TF32X3: the operands are 4-byte
+// TF32, so each GEMM runs in two K halves of 64.  NB = 1: a 6-qubit gate, one GEMM per slab; for
+// BF16 its E images stay in shared memory for the whole launch.  NB = 4: a 7-qubit gate (see
+// below), four GEMMs per slab into four TMEM accumulators.  Whenever E is not resident, its
+// (half-)images are copied from global memory (L2) by bulk TMA copies completing on an
+// mbarrier, one block or half at a time.
+template <int MODE, int NB>
 __global__ void __launch_bounds__(kThreads, 1)
     tc_kernel(float2 *__restrict__ state, const DevTc *__restrict__ d_tc,
                    const unsigned char *__restrict__ images, uint64_t nslabs, int *status)
@@ -195,31 +213,33 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t bar = saddr(&K.mbar);
 
+    const uint32_t bbar = saddr(&K.bbar);
     if (tid == 0) {
         K.tc = *d_tc;
         mbar_init(bar, 1);
+        mbar_init(bbar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
+    constexpr uint32_t kCols = uint32_t(kTcK) * NB;  // one 128-column FP32 accumulator per GEMM
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(&K.tmem)),
-                     "r"(uint32_t(kTcK))
+                     "r"(kCols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     constexpr bool kTf32 = MODE == QS_TC_TF32X3;
     constexpr int kParts = kTf32 ? 2 : 1;
+    constexpr bool kResident = !kTf32 && NB == 1;
     const unsigned char *img = images + d_tc->img;
-    // E half h of part hi / lo (TF32: [hi h0 | hi h1 | lo h0 | lo h1], 32 KiB each) -> B region
-    auto load_b = [&](int h) {
-        const unsigned char *src_hi = img + h * kOpBytes, *src_lo = img + (2 + h) * kOpBytes;
-        const uint32_t dhi = saddr(base + kOffBhi), dlo = saddr(base + kOffBlo);
-        for (uint32_t v = tid; v < kOpBytes / 16; v += kThreads) {
-            cp_async16(dhi + 16 * v, src_hi + 16 * v);
-            cp_async16(dlo + 16 * v, src_lo + 16 * v);
-        }
-        cp_async_commit();
+    // thread 0: bulk-copy half h of E block eb (per block: hi halves, then lo halves, 32 KiB each)
+    // into the B region; the B region must be free (the previous GEMM has completed)
+    auto load_b = [&](int eb, int h) {
+        const unsigned char *blk = img + size_t(eb) * (2 * kParts) * kOpBytes;
+        mbar_expect_tx(bbar, 2 * kOpBytes);
+        bulk_g2s(saddr(base + kOffBhi), blk + h * kOpBytes, kOpBytes, bbar);
+        bulk_g2s(saddr(base + kOffBlo), blk + (kParts + h) * kOpBytes, kOpBytes, bbar);
     };
-    if (!kTf32) {
+    if (kResident) {
         // resident E_hi / E_lo images (64 KiB contiguous in global memory)
         const uint32_t dst = saddr(base + kOffBhi);
         for (uint32_t v = tid; v < (2 * kOpBytes) / 16; v += kThreads) cp_async16(dst + 16 * v, img + 16 * v);
@@ -278,101 +298,144 @@ __global__ void __launch_bounds__(kThreads, 1)
     // Results go to the operand region A (64 KiB, free once the MMAs have completed) so that the
     // next slab can stream into the slab buffer while this one is multiplied and stored.
     float2 *res = reinterpret_cast<float2 *>(base + kOffAhi);
+    uint32_t bphase = 0;
+    bool b_pending = false;
     if (uint64_t(blockIdx.x) < nslabs) issue_load(slab_ptr(blockIdx.x));
     for (uint64_t s = blockIdx.x; s < nslabs && !failed; s += gridDim.x) {
         float2 *g = slab_ptr(s);
         cp_async_wait_all();
         __syncthreads();
         const bool more = s + gridDim.x < nslabs;
-        for (int h = 0; h < kParts; ++h) {
-            if (kTf32) load_b(h);  // the B region is free: the previous GEMM has completed
-            // split row m into hi / lo in the swizzled operand layout: thread (m, p) =
-            // (tid % 128, tid / 128) converts 16-byte chunks p*4 .. p*4+3 of the row's 16
-            const uint32_t m = tid & 127u, mo = K.moff[m], c16b = (tid >> 7) * kChunksPerThread;
-            if (!kTf32) {
+        for (int eb = 0; eb < NB && !failed; ++eb) {
+            for (int h = 0; h < kParts; ++h) {
+                if (!kResident && tid == 0) load_b(eb, h);  // lands while the split runs
+                b_pending = !kResident;
+                // BF16: one split per slab (the A operand serves all blocks); TF32: A holds one
+                // K half, so every (block, half) is split again
+                const bool do_split = kTf32 || eb == 0;
+                if (do_split) {
+                    // split row m into hi / lo in the swizzled operand layout: thread (m, p) =
+                    // (tid % 128, tid / 128) converts 16-byte chunks p*4 .. p*4+3 of the row's 16
+                    const uint32_t m = tid & 127u, mo = K.moff[m], c16b = (tid >> 7) * kChunksPerThread;
+                    if (!kTf32) {
 #pragma unroll
-                for (uint32_t c16 = c16b; c16 < c16b + kChunksPerThread; ++c16) {
-                    __nv_bfloat162 hv[4], lv[4];
+                        for (uint32_t c16 = c16b; c16 < c16b + kChunksPerThread; ++c16) {
+                            __nv_bfloat162 hv[4], lv[4];
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const float2 a = slab[mo | K.joff[c16 * 4 + q]];
-                        const __nv_bfloat16 hx = __float2bfloat16_rn(a.x), hy = __float2bfloat16_rn(a.y);
-                        hv[q] = __halves2bfloat162(hx, hy);
-                        lv[q] = __halves2bfloat162(__float2bfloat16_rn(a.x - __bfloat162float(hx)),
-                                                   __float2bfloat16_rn(a.y - __bfloat162float(hy)));
+                            for (int q = 0; q < 4; ++q) {
+                                const float2 a = slab[mo | K.joff[c16 * 4 + q]];
+                                const __nv_bfloat16 hx = __float2bfloat16_rn(a.x), hy = __float2bfloat16_rn(a.y);
+                                hv[q] = __halves2bfloat162(hx, hy);
+                                lv[q] = __halves2bfloat162(__float2bfloat16_rn(a.x - __bfloat162float(hx)),
+                                                           __float2bfloat16_rn(a.y - __bfloat162float(hy)));
+                            }
+                            const uint32_t off = op_chunk_offset(m, c16);
+                            *reinterpret_cast<uint4 *>(base + kOffAhi + off) = *reinterpret_cast<const uint4 *>(hv);
+                            *reinterpret_cast<uint4 *>(base + kOffAlo + off) = *reinterpret_cast<const uint4 *>(lv);
+                        }
+                    } else {
+                        // K half h holds targets j = 32h .. 32h + 31; a chunk is 2 amplitudes
+#pragma unroll
+                        for (uint32_t c16 = c16b; c16 < c16b + kChunksPerThread; ++c16) {
+                            const uint32_t j = 32u * uint32_t(h) + 2u * c16;
+                            const float2 a0 = slab[mo | K.joff[j]], a1 = slab[mo | K.joff[j + 1]];
+                            const float xs[4] = {a0.x, a0.y, a1.x, a1.y};
+                            uint32_t hv[4], lv[4];
+#pragma unroll
+                            for (int q = 0; q < 4; ++q) {
+                                hv[q] = to_tf32(xs[q]);
+                                lv[q] = to_tf32(xs[q] - __uint_as_float(hv[q]));
+                            }
+                            const uint32_t off = op_chunk_offset(m, c16);
+                            *reinterpret_cast<uint4 *>(base + kOffAhi + off) = make_uint4(hv[0], hv[1], hv[2], hv[3]);
+                            *reinterpret_cast<uint4 *>(base + kOffAlo + off) = make_uint4(lv[0], lv[1], lv[2], lv[3]);
+                        }
                     }
-                    const uint32_t off = op_chunk_offset(m, c16);
-                    *reinterpret_cast<uint4 *>(base + kOffAhi + off) = *reinterpret_cast<const uint4 *>(hv);
-                    *reinterpret_cast<uint4 *>(base + kOffAlo + off) = *reinterpret_cast<const uint4 *>(lv);
                 }
-            } else {
-                // K half h holds targets j = 32h .. 32h + 31; a chunk is 2 amplitudes (re, im, re, im)
-#pragma unroll
-                for (uint32_t c16 = c16b; c16 < c16b + kChunksPerThread; ++c16) {
-                    const uint32_t j = 32u * uint32_t(h) + 2u * c16;
-                    const float2 a0 = slab[mo | K.joff[j]], a1 = slab[mo | K.joff[j + 1]];
-                    const float xs[4] = {a0.x, a0.y, a1.x, a1.y};
-                    uint32_t hv[4], lv[4];
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        hv[q] = to_tf32(xs[q]);
-                        lv[q] = to_tf32(xs[q] - __uint_as_float(hv[q]));
+                const bool last_split = do_split && (kTf32 ? (eb == NB - 1 && h == kParts - 1) : true);
+                if (last_split) {
+                    __syncthreads();  // every split has read the slab buffer
+                    // prefetch this CTA's next slab into it; it lands while the GEMMs run
+                    if (more) issue_load(slab_ptr(s + gridDim.x));
+                }
+                if (!kResident) {
+                    const bool okb = mbar_wait_bounded(bbar, bphase);
+                    if (__syncthreads_or(!okb)) {  // the copy stays pending: waited for at exit
+                        if (tid == 0) atomicExch(status, QS_ETIMEOUT);
+                        failed = true;
+                        break;
                     }
-                    const uint32_t off = op_chunk_offset(m, c16);
-                    *reinterpret_cast<uint4 *>(base + kOffAhi + off) = make_uint4(hv[0], hv[1], hv[2], hv[3]);
-                    *reinterpret_cast<uint4 *>(base + kOffAlo + off) = make_uint4(lv[0], lv[1], lv[2], lv[3]);
+                    bphase ^= 1u;
+                    b_pending = false;
                 }
-            }
-            const bool last = h == kParts - 1;
-            if (last) {
-                __syncthreads();  // every split has read the slab buffer
-                // prefetch this CTA's next slab into it; it lands while the GEMM runs
-                if (more) issue_load(slab_ptr(s + gridDim.x));
-            }
-            if (kTf32) {
-                // the B half (committed before the prefetch) must have landed
-                if (last && more) cp_async_wait<1>();
-                else cp_async_wait<0>();
-            }
-            fence_proxy_async();
-            __syncthreads();
-            if (tid == 0) {
+                fence_proxy_async();
+                __syncthreads();
+                if (tid == 0) {
+                    tc_fence_after();
+                    // D_eb (+)= A_hi E_hi^T + A_hi E_lo^T + A_lo E_hi^T over 8 K-steps of 32 bytes
+                    const uint32_t ops[3][2] = {{sAhi, sBhi}, {sAhi, sBlo}, {sAlo, sBhi}};
+                    const uint32_t dcol = tmem + uint32_t(eb) * kTcK;
+#pragma unroll
+                    for (int pr = 0; pr < 3; ++pr)
+#pragma unroll
+                        for (int ks = 0; ks < 8; ++ks) {
+                            const uint32_t koff = (uint32_t(ks) >> 2) * (kTcRows * 128u) + (uint32_t(ks) & 3u) * 32u;
+                            const uint32_t acc = (h | pr | ks) ? 1u : 0u;
+                            if (kTf32) mma_tf32(dcol, smem_desc(ops[pr][0] + koff), smem_desc(ops[pr][1] + koff), acc);
+                            else mma_bf16(dcol, smem_desc(ops[pr][0] + koff), smem_desc(ops[pr][1] + koff), acc);
+                        }
+                    mma_commit(bar);
+                }
+                const bool ok = mbar_wait_bounded(bar, phase);
+                phase ^= 1u;
+                if (__syncthreads_or(!ok)) {
+                    if (tid == 0) atomicExch(status, QS_ETIMEOUT);
+                    mbar_wait_bounded(bar, phase ^ 1u);  // bounded grace for the MMAs in flight
+                    failed = true;
+                    break;
+                }
                 tc_fence_after();
-                // D (+)= A_hi E_hi^T + A_hi E_lo^T + A_lo E_hi^T over 8 K-steps of 32 bytes
-                const uint32_t ops[3][2] = {{sAhi, sBhi}, {sAhi, sBlo}, {sAlo, sBhi}};
-#pragma unroll
-                for (int pr = 0; pr < 3; ++pr)
-#pragma unroll
-                    for (int ks = 0; ks < 8; ++ks) {
-                        const uint32_t koff = (uint32_t(ks) >> 2) * (kTcRows * 128u) + (uint32_t(ks) & 3u) * 32u;
-                        const uint32_t acc = (h | pr | ks) ? 1u : 0u;
-                        if (kTf32) mma_tf32(tmem, smem_desc(ops[pr][0] + koff), smem_desc(ops[pr][1] + koff), acc);
-                        else mma_bf16(tmem, smem_desc(ops[pr][0] + koff), smem_desc(ops[pr][1] + koff), acc);
-                    }
-                mma_commit(bar);
             }
-            const bool ok = mbar_wait_bounded(bar, phase);
-            phase ^= 1u;
-            if (__syncthreads_or(!ok)) {
-                if (tid == 0) atomicExch(status, QS_ETIMEOUT);
-                mbar_wait_bounded(bar, phase ^ 1u);  // bounded grace for the MMAs in flight
-                failed = true;
-                break;
-            }
-            tc_fence_after();
         }
         if (failed) break;
         // epilogue: warp w reads rows 32q..32q+31 of its TMEM lane quarter q = w % 4, columns
         // 32h..32h+31 with h = w / 4, into the free operand region
         {
-            constexpr uint32_t kCols = kTcK / (kThreads / 128);
-            const uint32_t q4 = warp & 3u, m = q4 * 32 + lane, mo = K.moff[m], cb = (warp >> 2) * kCols;
+            constexpr uint32_t kColsW = kTcK / (kThreads / 128);
+            const uint32_t q4 = warp & 3u, m = q4 * 32 + lane, cb = (warp >> 2) * kColsW;
+            if (NB == 1) {
+                const uint32_t mo = K.moff[m];
 #pragma unroll 1
-            for (uint32_t c0 = cb; c0 < cb + kCols; c0 += 32) {
-                float r[32];
-                tmem_ld32(tmem + ((q4 * 32u) << 16) + c0, r);
+                for (uint32_t c0 = cb; c0 < cb + kColsW; c0 += 32) {
+                    float r[32];
+                    tmem_ld32(tmem + ((q4 * 32u) << 16) + c0, r);
 #pragma unroll
-                for (int q = 0; q < 16; ++q) res[mo | K.joff[c0 / 2 + q]] = make_float2(r[2 * q], r[2 * q + 1]);
+                    for (int q = 0; q < 16; ++q) res[mo | K.joff[c0 / 2 + q]] = make_float2(r[2 * q], r[2 * q + 1]);
+                }
+            } else {
+                // 7-qubit gate: row bit 6 is the gate's target 6.  Output row (t', rr) is
+                // D_{2t'}(0, rr) + D_{2t'+1}(1, rr): rows with bit 6 clear write their part of both
+                // outputs, then rows with bit 6 set add theirs.
+                const uint32_t hi = m >> 6, rr = m & 63u;
+                const uint32_t mo0 = K.moff[rr], mo1 = K.moff[rr | 64u];
+#pragma unroll 1
+                for (int ph = 0; ph < 2; ++ph) {
+                    if (uint32_t(ph) == hi) {
+#pragma unroll 1
+                        for (int t = 0; t < 2; ++t) {
+                            const uint32_t acc = 2u * uint32_t(t) + hi, mo = t ? mo1 : mo0;
+                            float r[32];
+                            tmem_ld32(tmem + ((q4 * 32u) << 16) + acc * kTcK + cb, r);
+#pragma unroll
+                            for (int q = 0; q < 16; ++q) {
+                                float2 &o = res[mo | K.joff[cb / 2 + q]];
+                                if (ph == 0) o = make_float2(r[2 * q], r[2 * q + 1]);
+                                else o = make_float2(o.x + r[2 * q], o.y + r[2 * q + 1]);
+                            }
+                        }
+                    }
+                    __syncthreads();
+                }
             }
         }
         tc_fence_before();
@@ -384,22 +447,26 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         __syncthreads();  // the operand region is rewritten by the next split
     }
+    if (b_pending) mbar_wait_bounded(bbar, bphase);  // a bulk copy issued before a timeout
     cp_async_wait_all();  // no copy may land after the CTA has left (timeout path)
     (void)failed;
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(uint32_t(kTcK))
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCols)
                      : "memory");
 }
 
 }  // namespace
 
-size_t tc_image_bytes(int mode) { return (mode == QS_TC_TF32X3 ? 4 : 2) * size_t(kOpBytes); }
+size_t tc_image_bytes(int mode, int width)
+{
+    return (mode == QS_TC_TF32X3 ? 4 : 2) * size_t(kOpBytes) * (width == 7 ? 4 : 1);
+}
 
 namespace {
-template <int MODE>
+template <int MODE, int NB>
 int launch_tc_t(const LaunchCtx &c, const DevTc *d_tc, const void *d_images, char *err, size_t errlen)
 {
     const size_t smem = kOffCtl + sizeof(TcCtl) + 1024;
@@ -407,13 +474,13 @@ int launch_tc_t(const LaunchCtx &c, const DevTc *d_tc, const void *d_images, cha
     int dev = 0;
     cudaGetDevice(&dev);
     if (attr_dev != dev) {
-        cudaFuncSetAttribute(tc_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(tc_kernel<MODE, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         attr_dev = dev;
     }
     const uint64_t nslabs = 1ull << (c.n - kTcSlabBits);
     uint64_t grid = uint64_t(num_sms());
     if (grid > nslabs) grid = nslabs;
-    tc_kernel<MODE><<<(unsigned)grid, kThreads, smem, (cudaStream_t)c.stream>>>(
+    tc_kernel<MODE, NB><<<(unsigned)grid, kThreads, smem, (cudaStream_t)c.stream>>>(
         reinterpret_cast<float2 *>(c.amp), d_tc, reinterpret_cast<const unsigned char *>(d_images), nslabs,
         device_status_ptr());
     cudaError_t e = cudaGetLastError();
@@ -432,8 +499,17 @@ int launch_tc(const LaunchCtx &c, const DevTc *d_tc, const DevTc &h, const void 
         snprintf(err, errlen, "tensor-core path: complex64 states only");
         return QS_EUNSUPPORTED;
     }
-    if (h.mode == QS_TC_BF16X3) return launch_tc_t<QS_TC_BF16X3>(c, d_tc, d_images, err, errlen);
-    if (h.mode == QS_TC_TF32X3) return launch_tc_t<QS_TC_TF32X3>(c, d_tc, d_images, err, errlen);
+    if (h.width != 6 && h.width != 7) {
+        snprintf(err, errlen, "tensor-core path: gate width %d (6 or 7)", h.width);
+        return QS_EINVAL;
+    }
+    const bool w7 = h.width == 7;
+    if (h.mode == QS_TC_BF16X3)
+        return w7 ? launch_tc_t<QS_TC_BF16X3, 4>(c, d_tc, d_images, err, errlen)
+                  : launch_tc_t<QS_TC_BF16X3, 1>(c, d_tc, d_images, err, errlen);
+    if (h.mode == QS_TC_TF32X3)
+        return w7 ? launch_tc_t<QS_TC_TF32X3, 4>(c, d_tc, d_images, err, errlen)
+                  : launch_tc_t<QS_TC_TF32X3, 1>(c, d_tc, d_images, err, errlen);
     snprintf(err, errlen, "tensor-core path: unknown mode %d", h.mode);
     return QS_EINVAL;
 }

@@ -148,7 +148,7 @@ void plan_features(const Plan &p, std::vector<float> &rows)
         case S_TC:
             f[5] = 1;
             f[6] = float(kTcSlabBits);
-            f[27] = float(kTcTargets);
+            f[27] = float(p.tcs[s.index].width);
             break;
         }
         rows.insert(rows.end(), f, f + QS_PLAN_FEATURES);

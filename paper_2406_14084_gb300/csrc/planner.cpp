@@ -1148,7 +1148,17 @@ void tc_images(const std::vector<cd> &U, std::vector<unsigned char> &out)
     std::memcpy(out.data() + base + hi.size() * 2, lo.data(), lo.size() * 2);
 }
 
-// A tensor-core step for dense gate g (6 targets) at the current layout.
+// The 64x64 block U[t' 64 + j'][t 64 + j] of a 7-qubit matrix (t', t = bit 6 of row, column).
+std::vector<cd> tc_block(const std::vector<cd> &U, int tr, int tc)
+{
+    std::vector<cd> B(size_t(64) * 64);
+    for (size_t j = 0; j < 64; ++j)
+        for (size_t l = 0; l < 64; ++l) B[j * 64 + l] = U[(size_t(tr) * 64 + j) * 128 + size_t(tc) * 64 + l];
+    return B;
+}
+
+// A tensor-core step for dense gate g (6 or 7 targets) at the current layout.  A 7th target
+// becomes row bit 6 of the slab's 128 x 64 matrix view.
 void emit_tc(Plan &plan, const CGate &g, const std::vector<int> &phys, int lo, int n, int mode)
 {
     std::set<int> S;
@@ -1169,20 +1179,30 @@ void emit_tc(Plan &plan, const CGate &g, const std::vector<int> &phys, int lo, i
     for (int p = 0; p < 64; ++p) local_of[p] = -1;
     for (int p = 0; p < lo; ++p) local_of[p] = p;
     for (size_t j = 0; j < hi.size(); ++j) local_of[hi[j]] = lo + (int)j;
+    const int width = (int)g.tq.size();
     uint32_t tmask = 0;
     std::vector<int> tphys;
-    for (size_t j = 0; j < g.tq.size(); ++j) {
-        T.tpos[j] = (uint8_t)local_of[phys[g.tq[j]]];
-        tmask |= 1u << T.tpos[j];
+    for (int j = 0; j < width; ++j) {
+        const uint8_t l = (uint8_t)local_of[phys[g.tq[j]]];
+        if (j < kTcTargets) T.tpos[j] = l;
+        tmask |= 1u << l;
         tphys.push_back(phys[g.tq[j]]);
     }
     int m = 0;
     for (int l = 0; l < kTcSlabBits; ++l)
         if (!(tmask >> l & 1)) T.mpos[m++] = (uint8_t)l;
+    if (width == 7) T.mpos[m++] = (uint8_t)local_of[phys[g.tq[6]]];
     T.img = (uint32_t)plan.tc_images.size();
     T.mode = mode;
-    if (mode == QS_TC_TF32X3) tc_images_tf32(g.m, plan.tc_images);
-    else tc_images(g.m, plan.tc_images);
+    T.width = width;
+    auto images = [&](const std::vector<cd> &U) {
+        if (mode == QS_TC_TF32X3) tc_images_tf32(U, plan.tc_images);
+        else tc_images(U, plan.tc_images);
+    };
+    if (width == 7)
+        for (int b = 0; b < 4; ++b) images(tc_block(g.m, b >> 1, b & 1));
+    else
+        images(g.m);
     plan.tc_coef.push_back((uint32_t)plan.coef.size());
     plan.coef.insert(plan.coef.end(), g.m.begin(), g.m.end());
     plan.tc_phys.push_back(tphys);
@@ -1383,20 +1403,21 @@ int build_plan(const std::vector<CGate> &gates_in, int n, qs_dtype dt, const qs_
             err = "the tensor-core path needs blocking and at least 13 qubits";
             return QS_EUNSUPPORTED;
         }
-        if (opt.tc_width != 0 && opt.tc_width != kTcTargets) {
-            err = "tensor-core blocks are built for 6 qubits only";
+        if (opt.tc_width != 0 && opt.tc_width != 6 && opt.tc_width != 7) {
+            err = "tensor-core blocks are 6 or 7 qubits wide";
             return QS_EUNSUPPORTED;
         }
     }
+    const int tcw = opt.tc_width == 7 ? 7 : kTcTargets;
     std::vector<char> is_tc;
     if (tc) {
-        // Alg. 2 level 3 with F = 6: merge greedily into dense blocks of at most 6 qubits; the
-        // products are FP64 on the host.  Blocks of 4+ qubits run on the tensor cores.  Diagonal
-        // runs are merged no wider than the blocks by default: wider tables could not join a
-        // 6-qubit block and would each cost a separate pass.
-        const int kdiag = opt.diag_bits > 0 ? std::min(opt.diag_bits, kMaxDiagBits) : kTcTargets;
+        // Alg. 2 level 3 with F = 6 or 7: merge greedily into dense blocks of at most F qubits;
+        // the products are FP64 on the host.  Blocks of 4+ qubits run on the tensor cores (7-qubit
+        // blocks as such, narrower ones widened to 6).  Diagonal runs are merged no wider than the
+        // blocks by default: wider tables could not join a block and would each cost a pass.
+        const int kdiag = opt.diag_bits > 0 ? std::min(opt.diag_bits, kMaxDiagBits) : tcw;
         gates = fuse_pass(gates, kdiag, 0, false, true, dt);
-        gates = fuse_pass(gates, kdiag, kTcTargets, true, false, dt);
+        gates = fuse_pass(gates, kdiag, tcw, true, false, dt);
         for (const CGate &g : gates) is_tc.push_back(g.cls == C_DENSE && g.tq.size() >= 4);
     } else if (opt.fuse_width > 0) {
         const bool euler = opt.euler != 1;
@@ -1461,7 +1482,8 @@ int build_plan(const std::vector<CGate> &gates_in, int n, qs_dtype dt, const qs_
         while (first < gates.size() && done[first]) ++first;
         if (first >= gates.size()) break;
         if (is_tc[first]) {
-            emit_tc(plan, pad_to_tc(gates[first], n, phys), phys, lo, n, opt.tc);
+            const CGate &g = gates[first];
+            emit_tc(plan, g.tq.size() == 7 ? g : pad_to_tc(g, n, phys), phys, lo, n, opt.tc);
             done[first] = 1;
             stalls = 0;
             continue;

@@ -112,10 +112,12 @@ struct DevStage {
 int num_sms();
 
 // Tensor-core wide gate (complex64 states).  A TC step is a slab pass over slabs of 2^13
-// amplitudes whose local bits are the 6 target bits (tpos, the K index of the GEMM) and 7 row
-// bits (mpos, the M index).  The operand images are the real embedding of the 64x64 unitary
-// split into hi and lo parts, pre-laid-out on the host in the 128-byte-swizzled K-major layout
-// of the tensor-core shared-memory descriptors.
+// amplitudes whose local bits are 6 target bits (tpos, the K index of the GEMM) and 7 row bits
+// (mpos, the M index).  The operand images are the real embedding of the 64x64 unitary split
+// into hi and lo parts, pre-laid-out on the host in the 128-byte-swizzled K-major layout of the
+// tensor-core shared-memory descriptors.  A 7-qubit gate (width 7) puts its 7th target on row
+// bit 6 (mpos[6]) and carries four such images, one per 64x64 block U[t' 64 + j'][t 64 + j]
+// (t', t = the 7th target bit of output and input), in the order (t', t) = 00, 01, 10, 11.
 constexpr int kTcTargets = 6;
 constexpr int kTcSlabBits = 13;
 constexpr int kTcRows = 128;    // GEMM M per slab
@@ -126,8 +128,9 @@ struct DevTc {
     uint8_t mpos[8];             // slab-local bit of row-index bit j
     uint32_t img;                // byte offset of this gate's operand images
     int32_t mode;                // QS_TC_BF16X3 or QS_TC_TF32X3
+    int32_t width;               // 6 or 7 targets
 };
-size_t tc_image_bytes(int mode);  // bytes of the hi+lo B images of one gate
+size_t tc_image_bytes(int mode, int width);  // bytes of the hi+lo B images of one gate
 
 // Launch entry points implemented in the .cu files (host side, stream-ordered).
 // `coef` points to the plan's coefficient pool already converted to the state precision.

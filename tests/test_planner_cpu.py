@@ -222,14 +222,25 @@ def test_fault_injection_on_host(monkeypatch):
     assert "injected" in str(e.value)
 
 
+@pytest.mark.parametrize("width", [6, 7])
 @pytest.mark.parametrize("mode", [qs.QS_TC_BF16X3, qs.QS_TC_TF32X3])
 @pytest.mark.parametrize("n", [13, 15])
-def test_tensor_core_plans_match_oracle(n, mode):
-    """Tensor-core mode fuses into <= 6-qubit dense blocks (4+ qubit blocks padded to 6 run as
-    tensor-core steps); the listing carries the FP64 fused matrices, replayed on the oracle."""
+def test_tensor_core_plans_match_oracle(n, mode, width):
+    """Tensor-core mode fuses into dense blocks of at most 6 or 7 qubits (4+ qubit blocks run as
+    tensor-core steps: 7-qubit blocks as such, narrower ones padded to 6); the listing carries
+    the FP64 fused matrices, replayed on the oracle."""
     gates = W.layered(n, 4, 11) + W.random_circuit(n, 40, 12, ALL)
-    info, stats = check_plan(gates, n, qs.options(tc=mode, dtype=qs.QS_C64))
+    opts = qs.options(tc=mode, dtype=qs.QS_C64, tc_width=width)
+    info, stats = check_plan(gates, n, opts)
     assert info["tc_gates"] > 0
+    p = qs.qs_fuse(gates, n, opts)
+    try:
+        widths = [int(l.split()[2]) for l in qs.qs_plan_dump(p).splitlines() if l.startswith("OP DENSE")]
+    finally:
+        qs.qs_plan_destroy(p)
+    if width == 7:
+        assert 7 in widths
+    assert max(widths) == width
 
 
 def test_tensor_core_mode_rejections():
@@ -241,7 +252,7 @@ def test_tensor_core_mode_rejections():
         qs.qs_fuse(W.layered(10, 2, 1), 10, qs.options(tc=qs.QS_TC_BF16X3, dtype=qs.QS_C64))
     assert e.value.status == qs.QS_EUNSUPPORTED
     with pytest.raises(qs.QsError) as e:
-        qs.qs_fuse(g, 14, qs.options(tc=qs.QS_TC_TF32X3, dtype=qs.QS_C64, tc_width=7))
+        qs.qs_fuse(g, 14, qs.options(tc=qs.QS_TC_TF32X3, dtype=qs.QS_C64, tc_width=8))
     assert e.value.status == qs.QS_EUNSUPPORTED
 
 
