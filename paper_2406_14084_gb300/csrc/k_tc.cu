@@ -14,18 +14,22 @@
 // Per slab: 16-byte cp.async gather of the slab -> FP32-to-BF16 hi/lo split into the
 // 128-byte-swizzled K-major operand layout -> 24 tcgen05.mma (3 products x 8 K-steps of 16)
 // issued by one thread into a 128-lane x 128-column FP32 accumulator in TMEM ->
-// tcgen05.commit to an mbarrier -> tcgen05.ld of the accumulator by the 4 warps (warp w owns
-// TMEM lanes 32w..32w+31 = rows) -> into the (now free) A operand region -> 16-byte stores.
-// The next slab's gather is issued as soon as the split has read the slab buffer, so it
-// overlaps the MMAs, the accumulator read-back and the stores.  The E operand stays in shared
-// memory for the whole launch.  Every mbarrier wait is bounded; on expiry the CTA
-// records QS_ETIMEOUT, releases its tensor memory and exits.
+// tcgen05.commit to an mbarrier -> tcgen05.ld of the accumulator by the 16 warps (four per TMEM
+// lane quarter) -> into the (now free) operand region -> 16-byte stores.  The next slab's
+// gather is issued as soon as the split has read the slab buffer, so it overlaps the MMAs, the
+// accumulator read-back and the stores.  Every mbarrier wait is bounded; on expiry the CTA
+// records QS_ETIMEOUT, waits (bounded) for its copies in flight, releases its tensor memory
+// and exits.
 //
 // TF32 x 3 mode (kind::tf32): the same three products with TF32 parts (10 stored mantissa bits
 // each, so hi + lo carries about 22 bits against BF16's 16).  The 4-byte operands take twice the
-// space, so each slab is multiplied in two K halves of 64 (targets 0..31, then 32..63), both
-// accumulating into the same TMEM columns; the E half-images (hi and lo, 32 KiB each) are copied
-// from global memory (L2-resident) before each half.
+// space, so each slab is split and multiplied in two K halves of 64 (targets 0..31, then
+// 32..63), both accumulating into the same TMEM columns.
+//
+// 7-qubit gates: the 7th target is row bit 6 of S, and the 128x128 unitary is applied as its
+// four 64x64 blocks in transposed form (E as the M = 128 operand, each half of S as an N = 64
+// operand; see the kernel).  E images that do not stay in shared memory (TF32, 7 qubits) are
+// streamed from L2 by bulk copies, double-buffered.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -47,8 +51,9 @@ constexpr uint32_t kOffAhi = kSlabBytes, kOffAlo = kOffAhi + kOpBytes, kOffBhi =
 constexpr uint32_t kWaitLimit = 1u << 24;
 
 struct TcCtl {
-    unsigned long long mbar;  // MMA completion
-    unsigned long long bbar;  // E-image bulk copies landed
+    unsigned long long mbar;      // all MMAs issued so far completed (every thread waits)
+    unsigned long long full[2];   // E chunk buffer b: bulk copies landed (thread 0 waits)
+    unsigned long long mdone[2];  // E chunk buffer b: its MMAs completed (thread 0 waits)
     uint32_t tmem;
     uint32_t pad;
     DevTc tc;
@@ -134,24 +139,29 @@ constexpr uint32_t kIdescBf16 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t(
                                 ((uint32_t(kTcRows) >> 4) << 24);
 constexpr uint32_t kIdescTf32 = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t(kTcK) >> 3) << 17) |
                                 ((uint32_t(kTcRows) >> 4) << 24);
+// the same with N = 64 (7-qubit blocks: operand B is the 64 slab rows of one 7th-bit value)
+constexpr uint32_t kIdescBf16N64 = (1u << 4) | (1u << 7) | (1u << 10) | ((64u >> 3) << 17) | ((uint32_t(kTcRows) >> 4) << 24);
+constexpr uint32_t kIdescTf32N64 = (1u << 4) | (2u << 7) | (2u << 10) | ((64u >> 3) << 17) | ((uint32_t(kTcRows) >> 4) << 24);
 
-__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accumulate)
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate)
 {
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
         "setp.ne.b32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
-        "l"(adesc), "l"(bdesc), "r"(kIdescBf16), "r"(accumulate)
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
         : "memory");
 }
 
-__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accumulate)
+__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate)
 {
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
         "setp.ne.b32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
-        "l"(adesc), "l"(bdesc), "r"(kIdescTf32), "r"(accumulate)
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
         : "memory");
 }
 
@@ -187,6 +197,11 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&r)[32])
     for (int i = 0; i < 32; ++i) r[i] = __uint_as_float(u[i]);
 }
 
+// Result-buffer slot of slab amplitude x for 7-qubit gates: bits 0-3 XORed with bits 4-7, 8-11
+// and 12 (an involution).  Their read-back writes 16 target values of one row per instruction;
+// with the targets on slab bits 4 and up these would share one bank group unswizzled.
+__device__ __forceinline__ uint32_t res_swz(uint32_t x) { return x ^ (((x >> 4) ^ (x >> 8) ^ (x >> 12)) & 15u); }
+
 // Byte offset of element (row, k) of a 128-row BF16 operand in the swizzled K-major layout:
 // K is split into 128-byte atoms (64 elements) stored one after the other for all rows.
 __device__ __forceinline__ uint32_t op_chunk_offset(uint32_t row, uint32_t chunk16)
@@ -195,50 +210,59 @@ __device__ __forceinline__ uint32_t op_chunk_offset(uint32_t row, uint32_t chunk
     return kb * (kTcRows * 128u) + row * 128u + ((c ^ (row & 7u)) << 4);
 }
 
-// MODE = QS_TC_BF16X3: each GEMM is over K = 128.  MODE = QS_TC_TF32X3: the operands are 4-byte
-// TF32, so each GEMM runs in two K halves of 64.  NB = 1: a 6-qubit gate, one GEMM per slab; for
-// BF16 its E images stay in shared memory for the whole launch.  NB = 4: a 7-qubit gate (see
-// below), four GEMMs per slab into four TMEM accumulators.  Whenever E is not resident, its
-// (half-)images are copied from global memory (L2) by bulk TMA copies completing on an
-// mbarrier, one block or half at a time.
+// The kernel.  MODE = QS_TC_BF16X3 (kind::f16, K = 16 per instruction) or QS_TC_TF32X3
+// (kind::tf32, K = 8; the 4-byte operands hold one K half of 64 at a time, so the slab is split
+// and multiplied in two halves).  NB = 1: a 6-qubit gate, D (rows x 128) = S E^T with the slab
+// matrix S as operand A.  NB = 4: a 7-qubit gate whose 7th target is row bit 6; with t', t the
+// 7th bit of output and input and S_t the 64 rows with row bit 6 = t, the transposed products
+//     D_t'^T (128 x 64) = sum_t E_t't S_t^T
+// take E as operand A (M = 128 output reals) and S_t as operand B (N = 64 rows starting at row
+// 64 t), accumulating both t in one TMEM accumulator per t' (columns 64 t' .. 64 t' + 63).
+//
+// E operand: for BF16 x 3 with NB = 1 the hi and lo images (64 KiB) stay in shared memory for
+// the whole launch.  Otherwise E is streamed from global memory (L2-resident) in chunks of one
+// 128-byte K atom (16 KiB hi + 16 KiB lo) by bulk copies into two alternating buffers: chunk
+// c + 1 is copied while chunk c is multiplied, and the stream runs on across slabs, so the
+// first chunks of the next slab land during the read-back and stores of the current one.
+// Chunk order within a slab: K half h, then E block eb (= 2 t' + t), then atom a of the half.
 template <int MODE, int NB>
 __global__ void __launch_bounds__(kThreads, 1)
     tc_kernel(float2 *__restrict__ state, const DevTc *__restrict__ d_tc,
-                   const unsigned char *__restrict__ images, uint64_t nslabs, int *status)
+              const unsigned char *__restrict__ images, uint64_t nslabs, int *status)
 {
+    constexpr bool kTf32 = MODE == QS_TC_TF32X3;
+    constexpr int kParts = kTf32 ? 2 : 1;               // K halves per slab
+    constexpr bool kResident = !kTf32 && NB == 1;
+    constexpr int kChunks = kParts * NB * 2;             // E chunks per slab
+    constexpr uint32_t kAtom = kTcRows * 128u;           // one 128-row K atom: 16 KiB
+    constexpr uint32_t kAtoms = 2u * kParts;             // K atoms of one E block
+    constexpr uint32_t kCols = uint32_t(kTcK);           // TMEM columns: one 128-column accumulator
+    constexpr uint32_t kIdesc = NB == 1 ? (kTf32 ? kIdescTf32 : kIdescBf16) : (kTf32 ? kIdescTf32N64 : kIdescBf16N64);
+
     extern __shared__ unsigned char smem_raw[];
     unsigned char *base = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     float2 *slab = reinterpret_cast<float2 *>(base);
     TcCtl &K = *reinterpret_cast<TcCtl *>(base + kOffCtl);
     const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t bar = saddr(&K.mbar);
+    const uint32_t full0 = saddr(&K.full[0]), mdone0 = saddr(&K.mdone[0]);  // [1] at +8
 
-    const uint32_t bbar = saddr(&K.bbar);
     if (tid == 0) {
         K.tc = *d_tc;
         mbar_init(bar, 1);
-        mbar_init(bbar, 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(full0 + 8u * b, 1);
+            mbar_init(mdone0 + 8u * b, 1);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    constexpr uint32_t kCols = uint32_t(kTcK) * NB;  // one 128-column FP32 accumulator per GEMM
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(&K.tmem)),
                      "r"(kCols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    constexpr bool kTf32 = MODE == QS_TC_TF32X3;
-    constexpr int kParts = kTf32 ? 2 : 1;
-    constexpr bool kResident = !kTf32 && NB == 1;
     const unsigned char *img = images + d_tc->img;
-    // thread 0: bulk-copy half h of E block eb (per block: hi halves, then lo halves, 32 KiB each)
-    // into the B region; the B region must be free (the previous GEMM has completed)
-    auto load_b = [&](int eb, int h) {
-        const unsigned char *blk = img + size_t(eb) * (2 * kParts) * kOpBytes;
-        mbar_expect_tx(bbar, 2 * kOpBytes);
-        bulk_g2s(saddr(base + kOffBhi), blk + h * kOpBytes, kOpBytes, bbar);
-        bulk_g2s(saddr(base + kOffBlo), blk + (kParts + h) * kOpBytes, kOpBytes, bbar);
-    };
     if (kResident) {
         // resident E_hi / E_lo images (64 KiB contiguous in global memory)
         const uint32_t dst = saddr(base + kOffBhi);
@@ -274,8 +298,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 
     const int vps_log = lo - 1;  // 16-byte vectors per segment (complex64: 2 per vector)
     const uint32_t nvec = 1u << (kTcSlabBits - 1);
-    const uint32_t sAhi = saddr(base + kOffAhi), sAlo = saddr(base + kOffAlo);
-    const uint32_t sBhi = saddr(base + kOffBhi), sBlo = saddr(base + kOffBlo);
+    const uint32_t sS[2] = {saddr(base + kOffAhi), saddr(base + kOffAlo)};  // slab operand hi, lo
     uint32_t phase = 0;
     bool failed = false;
 
@@ -295,146 +318,174 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         cp_async_commit();
     };
+
+    // ---- the E stream, driven by warp 0 (lane 0 issues the copies and MMAs; the whole warp
+    // waits, so that no lane of it sits in another wait meanwhile): chunk c of this CTA's
+    // sequence goes to buffer c & 1
+    const uint64_t nmine = uint64_t(blockIdx.x) < nslabs ? (nslabs - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    const uint64_t total = kResident ? 0 : nmine * kChunks;
+    uint64_t c_next = 0;                 // next chunk to multiply
+    uint64_t c_issued = 0, c_landed = 0; // chunks whose copies were issued / waited for
+    uint32_t fph = 0, mph = 0;           // per-buffer parities (bit b)
+    bool ok0 = true;                     // warp 0: every wait so far succeeded
+    // chunk = K atom a of E block eb, hi then lo: one contiguous 32 KiB bulk copy
+    auto chunk_load = [&](uint64_t c) {
+        const uint32_t cl = uint32_t(c % kChunks), b = uint32_t(c & 1);
+        const uint32_t h = cl / (NB * 2), eb = (cl >> 1) % NB, a = 2 * h + (cl & 1);
+        const unsigned char *src = img + size_t(eb * kAtoms + a) * 2 * kAtom;
+        mbar_expect_tx(full0 + 8u * b, 2 * kAtom);
+        bulk_g2s(saddr(base + kOffBhi) + b * 2 * kAtom, src, 2 * kAtom, full0 + 8u * b);
+    };
+    if (warp == 0 && total > 0) {
+        if (lane == 0) chunk_load(0);
+        c_issued = 1;
+    }
+    // multiply chunk c_next (warp 0): refill the other buffer once its chunk's MMAs are done,
+    // wait for this chunk's copy, issue 3 products x 4 K-steps
+    auto chunk_mma = [&]() {
+        const uint64_t c = c_next++;
+        const uint32_t cl = uint32_t(c % kChunks), b = uint32_t(c & 1);
+        const uint32_t h = cl / (NB * 2), eb = (cl >> 1) % NB, ah = cl & 1;
+        uint32_t bhi;
+        if (kResident) {
+            bhi = saddr(base + kOffBhi) + ah * 2 * kAtom;  // the resident image: atom ah
+        } else {
+            if (!ok0) return;
+            if (c >= 1) {
+                const uint32_t pb = b ^ 1u;
+                ok0 = __all_sync(0xffffffffu, mbar_wait_bounded(mdone0 + 8u * pb, (mph >> pb) & 1u));
+                mph ^= 1u << pb;
+                if (!ok0) return;
+            }
+            if (c + 1 < total) {
+                if (lane == 0) chunk_load(c + 1);
+                __syncwarp();
+                c_issued = c + 2;
+            }
+            ok0 = __all_sync(0xffffffffu, mbar_wait_bounded(full0 + 8u * b, (fph >> b) & 1u));
+            if (!ok0) return;  // the copy stays pending: waited for at exit
+            fph ^= 1u << b;
+            c_landed = c + 1;
+            bhi = saddr(base + kOffBhi) + b * 2 * kAtom;
+        }
+        if (lane != 0) return;
+        tc_fence_after();
+        const uint32_t ehl[2] = {bhi, bhi + kAtom};
+        // (slab part, E part) of the three products: hi.hi, hi.lo, lo.hi
+        const uint32_t pr_s[3] = {0, 0, 1}, pr_e[3] = {0, 1, 0};
+        const uint32_t tp = eb >> 1, t = eb & 1;
+#pragma unroll
+        for (int pr = 0; pr < 3; ++pr)
+#pragma unroll
+            for (uint32_t ks = 0; ks < 4; ++ks) {
+                const uint32_t soff = ah * kAtom + ks * 32u, eoff = ks * 32u;
+                if (NB == 1) {
+                    const uint32_t acc = (h | ah | uint32_t(pr) | ks) ? 1u : 0u;
+                    const uint64_t ad = smem_desc(sS[pr_s[pr]] + soff), bd = smem_desc(ehl[pr_e[pr]] + eoff);
+                    if (kTf32) mma_tf32(tmem, ad, bd, kIdesc, acc);
+                    else mma_bf16(tmem, ad, bd, kIdesc, acc);
+                } else {
+                    const uint32_t acc = (t | h | ah | uint32_t(pr) | ks) ? 1u : 0u;
+                    const uint64_t ad = smem_desc(ehl[pr_e[pr]] + eoff), bd = smem_desc(sS[pr_s[pr]] + soff + t * 8192u);
+                    if (kTf32) mma_tf32(tmem + tp * 64u, ad, bd, kIdesc, acc);
+                    else mma_bf16(tmem + tp * 64u, ad, bd, kIdesc, acc);
+                }
+            }
+        if (!kResident) mma_commit(mdone0 + 8u * b);
+    };
+
     // Results go to the operand region A (64 KiB, free once the MMAs have completed) so that the
     // next slab can stream into the slab buffer while this one is multiplied and stored.
     float2 *res = reinterpret_cast<float2 *>(base + kOffAhi);
-    uint32_t bphase = 0;
-    bool b_pending = false;
-    if (uint64_t(blockIdx.x) < nslabs) issue_load(slab_ptr(blockIdx.x));
+    if (nmine > 0) issue_load(slab_ptr(blockIdx.x));
     for (uint64_t s = blockIdx.x; s < nslabs && !failed; s += gridDim.x) {
         float2 *g = slab_ptr(s);
         cp_async_wait_all();
         __syncthreads();
-        const bool more = s + gridDim.x < nslabs;
-        for (int eb = 0; eb < NB && !failed; ++eb) {
-            for (int h = 0; h < kParts; ++h) {
-                if (!kResident && tid == 0) load_b(eb, h);  // lands while the split runs
-                b_pending = !kResident;
-                // BF16: one split per slab (the A operand serves all blocks); TF32: A holds one
-                // K half, so every (block, half) is split again
-                const bool do_split = kTf32 || eb == 0;
-                if (do_split) {
-                    // split row m into hi / lo in the swizzled operand layout: thread (m, p) =
-                    // (tid % 128, tid / 128) converts 16-byte chunks p*4 .. p*4+3 of the row's 16
-                    const uint32_t m = tid & 127u, mo = K.moff[m], c16b = (tid >> 7) * kChunksPerThread;
-                    if (!kTf32) {
+        for (int h = 0; h < kParts; ++h) {
+            // split row m into hi / lo in the swizzled K-major operand layout: thread (m, p) =
+            // (tid % 128, tid / 128) converts 16-byte chunks p*4 .. p*4+3 of the row's 16
+            const uint32_t m = tid & 127u, mo = K.moff[m], c16b = (tid >> 7) * kChunksPerThread;
+            if (!kTf32) {
 #pragma unroll
-                        for (uint32_t c16 = c16b; c16 < c16b + kChunksPerThread; ++c16) {
-                            __nv_bfloat162 hv[4], lv[4];
+                for (uint32_t c16 = c16b; c16 < c16b + kChunksPerThread; ++c16) {
+                    __nv_bfloat162 hv[4], lv[4];
 #pragma unroll
-                            for (int q = 0; q < 4; ++q) {
-                                const float2 a = slab[mo | K.joff[c16 * 4 + q]];
-                                const __nv_bfloat16 hx = __float2bfloat16_rn(a.x), hy = __float2bfloat16_rn(a.y);
-                                hv[q] = __halves2bfloat162(hx, hy);
-                                lv[q] = __halves2bfloat162(__float2bfloat16_rn(a.x - __bfloat162float(hx)),
-                                                           __float2bfloat16_rn(a.y - __bfloat162float(hy)));
-                            }
-                            const uint32_t off = op_chunk_offset(m, c16);
-                            *reinterpret_cast<uint4 *>(base + kOffAhi + off) = *reinterpret_cast<const uint4 *>(hv);
-                            *reinterpret_cast<uint4 *>(base + kOffAlo + off) = *reinterpret_cast<const uint4 *>(lv);
-                        }
-                    } else {
-                        // K half h holds targets j = 32h .. 32h + 31; a chunk is 2 amplitudes
-#pragma unroll
-                        for (uint32_t c16 = c16b; c16 < c16b + kChunksPerThread; ++c16) {
-                            const uint32_t j = 32u * uint32_t(h) + 2u * c16;
-                            const float2 a0 = slab[mo | K.joff[j]], a1 = slab[mo | K.joff[j + 1]];
-                            const float xs[4] = {a0.x, a0.y, a1.x, a1.y};
-                            uint32_t hv[4], lv[4];
-#pragma unroll
-                            for (int q = 0; q < 4; ++q) {
-                                hv[q] = to_tf32(xs[q]);
-                                lv[q] = to_tf32(xs[q] - __uint_as_float(hv[q]));
-                            }
-                            const uint32_t off = op_chunk_offset(m, c16);
-                            *reinterpret_cast<uint4 *>(base + kOffAhi + off) = make_uint4(hv[0], hv[1], hv[2], hv[3]);
-                            *reinterpret_cast<uint4 *>(base + kOffAlo + off) = make_uint4(lv[0], lv[1], lv[2], lv[3]);
-                        }
+                    for (int q = 0; q < 4; ++q) {
+                        const float2 a = slab[mo | K.joff[c16 * 4 + q]];
+                        const __nv_bfloat16 hx = __float2bfloat16_rn(a.x), hy = __float2bfloat16_rn(a.y);
+                        hv[q] = __halves2bfloat162(hx, hy);
+                        lv[q] = __halves2bfloat162(__float2bfloat16_rn(a.x - __bfloat162float(hx)),
+                                                   __float2bfloat16_rn(a.y - __bfloat162float(hy)));
                     }
-                }
-                const bool last_split = do_split && (kTf32 ? (eb == NB - 1 && h == kParts - 1) : true);
-                if (last_split) {
-                    __syncthreads();  // every split has read the slab buffer
-                    // prefetch this CTA's next slab into it; it lands while the GEMMs run
-                    if (more) issue_load(slab_ptr(s + gridDim.x));
-                }
-                if (!kResident) {
-                    const bool okb = mbar_wait_bounded(bbar, bphase);
-                    if (__syncthreads_or(!okb)) {  // the copy stays pending: waited for at exit
-                        if (tid == 0) atomicExch(status, QS_ETIMEOUT);
-                        failed = true;
-                        break;
-                    }
-                    bphase ^= 1u;
-                    b_pending = false;
-                }
-                fence_proxy_async();
-                __syncthreads();
-                if (tid == 0) {
-                    tc_fence_after();
-                    // D_eb (+)= A_hi E_hi^T + A_hi E_lo^T + A_lo E_hi^T over 8 K-steps of 32 bytes
-                    const uint32_t ops[3][2] = {{sAhi, sBhi}, {sAhi, sBlo}, {sAlo, sBhi}};
-                    const uint32_t dcol = tmem + uint32_t(eb) * kTcK;
-#pragma unroll
-                    for (int pr = 0; pr < 3; ++pr)
-#pragma unroll
-                        for (int ks = 0; ks < 8; ++ks) {
-                            const uint32_t koff = (uint32_t(ks) >> 2) * (kTcRows * 128u) + (uint32_t(ks) & 3u) * 32u;
-                            const uint32_t acc = (h | pr | ks) ? 1u : 0u;
-                            if (kTf32) mma_tf32(dcol, smem_desc(ops[pr][0] + koff), smem_desc(ops[pr][1] + koff), acc);
-                            else mma_bf16(dcol, smem_desc(ops[pr][0] + koff), smem_desc(ops[pr][1] + koff), acc);
-                        }
-                    mma_commit(bar);
-                }
-                const bool ok = mbar_wait_bounded(bar, phase);
-                phase ^= 1u;
-                if (__syncthreads_or(!ok)) {
-                    if (tid == 0) atomicExch(status, QS_ETIMEOUT);
-                    mbar_wait_bounded(bar, phase ^ 1u);  // bounded grace for the MMAs in flight
-                    failed = true;
-                    break;
-                }
-                tc_fence_after();
-            }
-        }
-        if (failed) break;
-        // epilogue: warp w reads rows 32q..32q+31 of its TMEM lane quarter q = w % 4, columns
-        // 32h..32h+31 with h = w / 4, into the free operand region
-        {
-            constexpr uint32_t kColsW = kTcK / (kThreads / 128);
-            const uint32_t q4 = warp & 3u, m = q4 * 32 + lane, cb = (warp >> 2) * kColsW;
-            if (NB == 1) {
-                const uint32_t mo = K.moff[m];
-#pragma unroll 1
-                for (uint32_t c0 = cb; c0 < cb + kColsW; c0 += 32) {
-                    float r[32];
-                    tmem_ld32(tmem + ((q4 * 32u) << 16) + c0, r);
-#pragma unroll
-                    for (int q = 0; q < 16; ++q) res[mo | K.joff[c0 / 2 + q]] = make_float2(r[2 * q], r[2 * q + 1]);
+                    const uint32_t off = op_chunk_offset(m, c16);
+                    *reinterpret_cast<uint4 *>(base + kOffAhi + off) = *reinterpret_cast<const uint4 *>(hv);
+                    *reinterpret_cast<uint4 *>(base + kOffAlo + off) = *reinterpret_cast<const uint4 *>(lv);
                 }
             } else {
-                // 7-qubit gate: row bit 6 is the gate's target 6.  Output row (t', rr) is
-                // D_{2t'}(0, rr) + D_{2t'+1}(1, rr): rows with bit 6 clear write their part of both
-                // outputs, then rows with bit 6 set add theirs.
-                const uint32_t hi = m >> 6, rr = m & 63u;
-                const uint32_t mo0 = K.moff[rr], mo1 = K.moff[rr | 64u];
-#pragma unroll 1
-                for (int ph = 0; ph < 2; ++ph) {
-                    if (uint32_t(ph) == hi) {
-#pragma unroll 1
-                        for (int t = 0; t < 2; ++t) {
-                            const uint32_t acc = 2u * uint32_t(t) + hi, mo = t ? mo1 : mo0;
-                            float r[32];
-                            tmem_ld32(tmem + ((q4 * 32u) << 16) + acc * kTcK + cb, r);
+                // K half h holds targets j = 32h .. 32h + 31; a chunk is 2 amplitudes
 #pragma unroll
-                            for (int q = 0; q < 16; ++q) {
-                                float2 &o = res[mo | K.joff[cb / 2 + q]];
-                                if (ph == 0) o = make_float2(r[2 * q], r[2 * q + 1]);
-                                else o = make_float2(o.x + r[2 * q], o.y + r[2 * q + 1]);
-                            }
-                        }
+                for (uint32_t c16 = c16b; c16 < c16b + kChunksPerThread; ++c16) {
+                    const uint32_t j = 32u * uint32_t(h) + 2u * c16;
+                    const float2 a0 = slab[mo | K.joff[j]], a1 = slab[mo | K.joff[j + 1]];
+                    const float xs[4] = {a0.x, a0.y, a1.x, a1.y};
+                    uint32_t hv[4], lv[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        hv[q] = to_tf32(xs[q]);
+                        lv[q] = to_tf32(xs[q] - __uint_as_float(hv[q]));
                     }
-                    __syncthreads();
+                    const uint32_t off = op_chunk_offset(m, c16);
+                    *reinterpret_cast<uint4 *>(base + kOffAhi + off) = make_uint4(hv[0], hv[1], hv[2], hv[3]);
+                    *reinterpret_cast<uint4 *>(base + kOffAlo + off) = make_uint4(lv[0], lv[1], lv[2], lv[3]);
+                }
+            }
+            if (h == kParts - 1) {
+                __syncthreads();  // every split has read the slab buffer
+                // prefetch this CTA's next slab into it; it lands while the GEMMs run
+                if (s + gridDim.x < nslabs) issue_load(slab_ptr(s + gridDim.x));
+            }
+            fence_proxy_async();
+            __syncthreads();
+            if (warp == 0) {
+                for (int k = 0; k < NB * 2; ++k) chunk_mma();
+                if (lane == 0) mma_commit(bar);  // arrives once every MMA issued so far has completed
+                __syncwarp();
+            }
+            const bool ok = mbar_wait_bounded(bar, phase);
+            phase ^= 1u;
+            if (__syncthreads_or(!ok || (tid == 0 && !ok0))) {
+                if (tid == 0) atomicExch(status, QS_ETIMEOUT);
+                if (!ok) mbar_wait_bounded(bar, phase ^ 1u);  // bounded grace for the MMAs in flight
+                failed = true;
+                break;
+            }
+            tc_fence_after();
+        }
+        if (failed) break;
+        // epilogue: warp w reads TMEM lane quarter q = w % 4 (lanes 32q .. 32q + 31), columns
+        // 32g .. 32g + 31 with g = w / 4, into the free operand region
+        {
+            const uint32_t q4 = warp & 3u, g4 = warp >> 2;
+            float r[32];
+            tmem_ld32(tmem + ((q4 * 32u) << 16) + 32u * g4, r);
+            if (NB == 1) {
+                // lane = slab row m, columns = output reals 2j + (re, im) for j = 16 g .. 16 g + 15
+                const uint32_t mo = K.moff[q4 * 32 + lane];
+#pragma unroll
+                for (int q = 0; q < 16; ++q) res[mo | K.joff[16 * g4 + q]] = make_float2(r[2 * q], r[2 * q + 1]);
+            } else {
+                // lane = output real 2j + c (j = 16 q + lane / 2), columns = rows rr0 .. rr0 + 31
+                // of output half t' = g / 2 (rr0 = 32 (g % 2)); lanes 2i, 2i + 1 swap halves so
+                // that each writes whole complex values
+                const uint32_t c = lane & 1u, jo = K.joff[16 * q4 + (lane >> 1)];
+                const uint32_t row0 = ((g4 >> 1) << 6) | ((g4 & 1u) << 5);
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    const float send = c ? r[i] : r[16 + i];
+                    const float recv = __shfl_xor_sync(0xffffffffu, send, 1);
+                    if (c == 0) res[res_swz(K.moff[row0 + i] | jo)] = make_float2(r[i], recv);
+                    else res[res_swz(K.moff[row0 + 16 + i] | jo)] = make_float2(recv, r[16 + i]);
                 }
             }
         }
@@ -443,13 +494,25 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (uint32_t v = tid; v < nvec; v += kThreads) {
             const uint32_t seg = v >> vps_log, w = v & ((1u << vps_log) - 1);
             const uint64_t so = K.seg_lo[seg & 63] | K.seg_hi[(seg >> 6) & 63];
-            __stcs(reinterpret_cast<float4 *>(g + so) + w, reinterpret_cast<const float4 *>(res)[v]);
+            float4 o;
+            if (NB == 1) {
+                o = reinterpret_cast<const float4 *>(res)[v];
+            } else {
+                const float2 a0 = res[res_swz(2 * v)], a1 = res[res_swz(2 * v + 1)];
+                o = make_float4(a0.x, a0.y, a1.x, a1.y);
+            }
+            __stcs(reinterpret_cast<float4 *>(g + so) + w, o);
         }
         __syncthreads();  // the operand region is rewritten by the next split
     }
-    if (b_pending) mbar_wait_bounded(bbar, bphase);  // a bulk copy issued before a timeout
-    cp_async_wait_all();  // no copy may land after the CTA has left (timeout path)
-    (void)failed;
+    // timeout path: no copy may land after the CTA has left
+    if (warp == 0)
+        for (uint64_t c = c_landed; c < c_issued; ++c) {
+            const uint32_t b = uint32_t(c & 1);
+            mbar_wait_bounded(full0 + 8u * b, (fph >> b) & 1u);
+            fph ^= 1u << b;
+        }
+    cp_async_wait_all();
     tc_fence_before();
     __syncthreads();
     tc_fence_after();

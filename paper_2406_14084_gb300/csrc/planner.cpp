@@ -1091,9 +1091,22 @@ float tf32_value(uint32_t u)
     return f;
 }
 
+// Image layout of one E matrix: per 128-byte K atom (128 rows x 128 bytes = 16 KiB per part),
+// the hi part then the lo part, so that the kernel fetches one atom of both parts with one
+// 32 KiB bulk copy.  `hi` and `lo` hold the parts atom after atom.
+void append_atoms(std::vector<unsigned char> &out, const unsigned char *hi, const unsigned char *lo, size_t part_bytes)
+{
+    const size_t atom = size_t(kTcRows) * 128;
+    const size_t base = out.size();
+    out.resize(base + 2 * part_bytes);
+    for (size_t a = 0; a * atom < part_bytes; ++a) {
+        std::memcpy(out.data() + base + 2 * a * atom, hi + a * atom, atom);
+        std::memcpy(out.data() + base + (2 * a + 1) * atom, lo + a * atom, atom);
+    }
+}
+
 // TF32 x 3 images: E = E_hi + E_lo in TF32 (from FP64), 4-byte elements in the same swizzled
-// K-major layout with 128-byte atoms of 32 elements; per part the four K atoms follow each other,
-// so K half h (atoms 2h, 2h + 1) is one contiguous 32 KiB block.  Order: hi, then lo.
+// K-major layout with 128-byte atoms of 32 elements (four K atoms).
 void tc_images_tf32(const std::vector<cd> &U, std::vector<unsigned char> &out)
 {
     const int K = kTcK, R = kTcK;
@@ -1115,10 +1128,8 @@ void tc_images_tf32(const std::vector<cd> &U, std::vector<unsigned char> &out)
                     lo[idx] = w;
                 }
         }
-    const size_t base = out.size();
-    out.resize(base + 2 * hi.size() * 4);
-    std::memcpy(out.data() + base, hi.data(), hi.size() * 4);
-    std::memcpy(out.data() + base + hi.size() * 4, lo.data(), lo.size() * 4);
+    append_atoms(out, reinterpret_cast<const unsigned char *>(hi.data()), reinterpret_cast<const unsigned char *>(lo.data()),
+                 hi.size() * 4);
 }
 
 void tc_images(const std::vector<cd> &U, std::vector<unsigned char> &out)
@@ -1142,10 +1153,8 @@ void tc_images(const std::vector<cd> &U, std::vector<unsigned char> &out)
                     lo[idx] = w;
                 }
         }
-    const size_t base = out.size();
-    out.resize(base + 2 * hi.size() * 2);
-    std::memcpy(out.data() + base, hi.data(), hi.size() * 2);
-    std::memcpy(out.data() + base + hi.size() * 2, lo.data(), lo.size() * 2);
+    append_atoms(out, reinterpret_cast<const unsigned char *>(hi.data()), reinterpret_cast<const unsigned char *>(lo.data()),
+                 hi.size() * 2);
 }
 
 // The 64x64 block U[t' 64 + j'][t 64 + j] of a 7-qubit matrix (t', t = bit 6 of row, column).
