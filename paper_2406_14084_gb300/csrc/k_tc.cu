@@ -28,8 +28,9 @@
 //
 // 7-qubit gates: the 7th target is row bit 6 of S, and the 128x128 unitary is applied as its
 // four 64x64 blocks in transposed form (E as the M = 128 operand, each half of S as an N = 64
-// operand; see the kernel).  E images that do not stay in shared memory (TF32, 7 qubits) are
-// streamed from L2 by bulk copies, double-buffered.
+// operand; see the kernel).  E images that do not stay in shared memory come from L2 by bulk
+// copies: for TF32 6-qubit gates one 64 KiB copy per K half, issued before that half's split;
+// for 7-qubit gates a stream of 32 KiB chunks through two buffers.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -220,11 +221,12 @@ __device__ __forceinline__ uint32_t op_chunk_offset(uint32_t row, uint32_t chunk
 // 64 t), accumulating both t in one TMEM accumulator per t' (columns 64 t' .. 64 t' + 63).
 //
 // E operand: for BF16 x 3 with NB = 1 the hi and lo images (64 KiB) stay in shared memory for
-// the whole launch.  Otherwise E is streamed from global memory (L2-resident) in chunks of one
-// 128-byte K atom (16 KiB hi + 16 KiB lo) by bulk copies into two alternating buffers: chunk
-// c + 1 is copied while chunk c is multiplied, and the stream runs on across slabs, so the
-// first chunks of the next slab land during the read-back and stores of the current one.
-// Chunk order within a slab: K half h, then E block eb (= 2 t' + t), then atom a of the half.
+// the whole launch.  For TF32 x 3 with NB = 1 the half of the image that a K half needs (two
+// atoms, 64 KiB) is copied in one bulk copy before that half's split.  For NB = 4 E is streamed
+// from global memory (L2-resident) in chunks of one 128-byte K atom (16 KiB hi + 16 KiB lo) by
+// bulk copies into two alternating buffers: chunk c + 1 is copied while chunk c is multiplied,
+// and the stream runs on across slabs.  Chunk order within a slab: K half h, then E block
+// eb (= 2 t' + t), then atom a of the half.
 template <int MODE, int NB>
 __global__ void __launch_bounds__(kThreads, 1)
     tc_kernel(float2 *__restrict__ state, const DevTc *__restrict__ d_tc,
@@ -233,7 +235,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     constexpr bool kTf32 = MODE == QS_TC_TF32X3;
     constexpr int kParts = kTf32 ? 2 : 1;               // K halves per slab
     constexpr bool kResident = !kTf32 && NB == 1;
-    constexpr int kChunks = kParts * NB * 2;             // E chunks per slab
+    // TF32 6-qubit: one 64 KiB copy per K half, issued before that half's split so that it
+    // lands while the split runs; 7-qubit: the two-buffer chunk stream
+    constexpr bool kHalfCopy = kTf32 && NB == 1;
+    constexpr bool kStream = !kResident && !kHalfCopy;
+    constexpr int kChunks = kParts * NB * 2;             // E chunks (K atoms) per slab
     constexpr uint32_t kAtom = kTcRows * 128u;           // one 128-row K atom: 16 KiB
     constexpr uint32_t kAtoms = 2u * kParts;             // K atoms of one E block
     constexpr uint32_t kCols = uint32_t(kTcK);           // TMEM columns: one 128-column accumulator
@@ -323,7 +329,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     // waits, so that no lane of it sits in another wait meanwhile): chunk c of this CTA's
     // sequence goes to buffer c & 1
     const uint64_t nmine = uint64_t(blockIdx.x) < nslabs ? (nslabs - 1 - blockIdx.x) / gridDim.x + 1 : 0;
-    const uint64_t total = kResident ? 0 : nmine * kChunks;
+    const uint64_t total = kStream ? nmine * kChunks : 0;
     uint64_t c_next = 0;                 // next chunk to multiply
     uint64_t c_issued = 0, c_landed = 0; // chunks whose copies were issued / waited for
     uint32_t fph = 0, mph = 0;           // per-buffer parities (bit b)
@@ -347,8 +353,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         const uint32_t cl = uint32_t(c % kChunks), b = uint32_t(c & 1);
         const uint32_t h = cl / (NB * 2), eb = (cl >> 1) % NB, ah = cl & 1;
         uint32_t bhi;
-        if (kResident) {
-            bhi = saddr(base + kOffBhi) + ah * 2 * kAtom;  // the resident image: atom ah
+        if (!kStream) {
+            if (!ok0) return;
+            bhi = saddr(base + kOffBhi) + ah * 2 * kAtom;  // atom ah of the resident image or the half
         } else {
             if (!ok0) return;
             if (c >= 1) {
@@ -391,7 +398,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     else mma_bf16(tmem + tp * 64u, ad, bd, kIdesc, acc);
                 }
             }
-        if (!kResident) mma_commit(mdone0 + 8u * b);
+        if (kStream) mma_commit(mdone0 + 8u * b);
     };
 
     // Results go to the operand region A (64 KiB, free once the MMAs have completed) so that the
@@ -403,6 +410,14 @@ __global__ void __launch_bounds__(kThreads, 1)
         cp_async_wait_all();
         __syncthreads();
         for (int h = 0; h < kParts; ++h) {
+            if (kHalfCopy && warp == 0) {  // every MMA so far has completed: the buffer is free
+                if (lane == 0) {
+                    mbar_expect_tx(full0, 4 * kAtom);
+                    bulk_g2s(saddr(base + kOffBhi), img + size_t(h) * 4 * kAtom, 4 * kAtom, full0);
+                }
+                __syncwarp();
+                ++c_issued;
+            }
             // split row m into hi / lo in the swizzled K-major operand layout: thread (m, p) =
             // (tid % 128, tid / 128) converts 16-byte chunks p*4 .. p*4+3 of the row's 16
             const uint32_t m = tid & 127u, mo = K.moff[m], c16b = (tid >> 7) * kChunksPerThread;
@@ -448,6 +463,13 @@ __global__ void __launch_bounds__(kThreads, 1)
             fence_proxy_async();
             __syncthreads();
             if (warp == 0) {
+                if (kHalfCopy && ok0) {
+                    ok0 = __all_sync(0xffffffffu, mbar_wait_bounded(full0, fph & 1u));
+                    if (ok0) {
+                        fph ^= 1u;
+                        c_landed = c_issued;
+                    }
+                }
                 for (int k = 0; k < NB * 2; ++k) chunk_mma();
                 if (lane == 0) mma_commit(bar);  // arrives once every MMA issued so far has completed
                 __syncwarp();
@@ -508,7 +530,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     // timeout path: no copy may land after the CTA has left
     if (warp == 0)
         for (uint64_t c = c_landed; c < c_issued; ++c) {
-            const uint32_t b = uint32_t(c & 1);
+            const uint32_t b = kHalfCopy ? 0u : uint32_t(c & 1);
             mbar_wait_bounded(full0 + 8u * b, (fph >> b) & 1u);
             fph ^= 1u << b;
         }
