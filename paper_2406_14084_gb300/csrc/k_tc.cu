@@ -198,9 +198,10 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&r)[32])
     for (int i = 0; i < 32; ++i) r[i] = __uint_as_float(u[i]);
 }
 
-// Result-buffer slot of slab amplitude x for 7-qubit gates: bits 0-3 XORed with bits 4-7, 8-11
-// and 12 (an involution).  Their read-back writes 16 target values of one row per instruction;
-// with the targets on slab bits 4 and up these would share one bank group unswizzled.
+// Result-buffer slot of slab amplitude x: bits 0-3 XORed with bits 4-7, 8-11 and 12 (an
+// involution).  A read-back instruction writes 32 values whose slab indices differ in 5 bits
+// (32 rows of one target value for 6-qubit gates, 16 target values of two rows for 7-qubit
+// gates); unswizzled, whenever those bits lie above bit 3 they all fall into one bank group.
 __device__ __forceinline__ uint32_t res_swz(uint32_t x) { return x ^ (((x >> 4) ^ (x >> 8) ^ (x >> 12)) & 15u); }
 
 // Byte offset of element (row, k) of a 128-row BF16 operand in the swizzled K-major layout:
@@ -495,7 +496,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 // lane = slab row m, columns = output reals 2j + (re, im) for j = 16 g .. 16 g + 15
                 const uint32_t mo = K.moff[q4 * 32 + lane];
 #pragma unroll
-                for (int q = 0; q < 16; ++q) res[mo | K.joff[16 * g4 + q]] = make_float2(r[2 * q], r[2 * q + 1]);
+                for (int q = 0; q < 16; ++q) res[res_swz(mo | K.joff[16 * g4 + q])] = make_float2(r[2 * q], r[2 * q + 1]);
             } else {
                 // lane = output real 2j + c (j = 16 q + lane / 2), columns = rows rr0 .. rr0 + 31
                 // of output half t' = g / 2 (rr0 = 32 (g % 2)); lanes 2i, 2i + 1 swap halves so
@@ -516,14 +517,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (uint32_t v = tid; v < nvec; v += kThreads) {
             const uint32_t seg = v >> vps_log, w = v & ((1u << vps_log) - 1);
             const uint64_t so = K.seg_lo[seg & 63] | K.seg_hi[(seg >> 6) & 63];
-            float4 o;
-            if (NB == 1) {
-                o = reinterpret_cast<const float4 *>(res)[v];
-            } else {
-                const float2 a0 = res[res_swz(2 * v)], a1 = res[res_swz(2 * v + 1)];
-                o = make_float4(a0.x, a0.y, a1.x, a1.y);
-            }
-            __stcs(reinterpret_cast<float4 *>(g + so) + w, o);
+            const float2 a0 = res[res_swz(2 * v)], a1 = res[res_swz(2 * v + 1)];
+            __stcs(reinterpret_cast<float4 *>(g + so) + w, make_float4(a0.x, a0.y, a1.x, a1.y));
         }
         __syncthreads();  // the operand region is rewritten by the next split
     }
