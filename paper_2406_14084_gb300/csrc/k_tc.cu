@@ -354,7 +354,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const uint32_t cl = uint32_t(c % kChunks), b = uint32_t(c & 1);
         const uint32_t h = cl / (NB * 2), eb = (cl >> 1) % NB, ah = cl & 1;
         uint32_t bhi;
-        if (!kStream) {
+        if constexpr (!kStream) {
             if (!ok0) return;
             bhi = saddr(base + kOffBhi) + ah * 2 * kAtom;  // atom ah of the resident image or the half
         } else {
