@@ -59,6 +59,7 @@ struct TcCtl {
     uint32_t pad;
     DevTc tc;
     uint64_t seg_lo[64], seg_hi[64];
+    uint64_t jg[64];     // offset in the state (from the slab's base) of target index j
     uint16_t joff[64];   // slab-local offset of target index j
     uint16_t moff[128];  // slab-local offset of row m
 };
@@ -302,6 +303,17 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     cp_async_wait_all();
     __syncthreads();
+    // state offset of a slab-local index: bits below lo stay, bit lo + i goes to hipos[i]; the
+    // bits of a row and of a target index are disjoint, so an amplitude's offset is the OR
+    for (uint32_t j = tid; j < 64; j += kThreads) {
+        const uint32_t x = K.joff[j];
+        K.jg[j] = K.seg_lo[(x >> lo) & 63] | K.seg_hi[(x >> (lo + 6)) & 63] | (x & ((1u << lo) - 1));
+    }
+    // 6-qubit gates whose 4 lowest row bits are the slab's lowest bits (the usual layout): a
+    // read-back instruction covers 32 rows of one target value = two whole 128-byte segments,
+    // so it stores straight to HBM; other layouts go through the swizzled result buffer
+    const bool direct = NB == 1 && lo >= 4 && K.moff[1] == 1 && K.moff[2] == 2 && K.moff[4] == 4 && K.moff[8] == 8;
+    __syncthreads();
 
     const int vps_log = lo - 1;  // 16-byte vectors per segment (complex64: 2 per vector)
     const uint32_t nvec = 1u << (kTcSlabBits - 1);
@@ -495,8 +507,14 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (NB == 1) {
                 // lane = slab row m, columns = output reals 2j + (re, im) for j = 16 g .. 16 g + 15
                 const uint32_t mo = K.moff[q4 * 32 + lane];
+                if (direct) {
+                    const uint64_t mg = K.seg_lo[(mo >> lo) & 63] | K.seg_hi[(mo >> (lo + 6)) & 63] | (mo & ((1u << lo) - 1));
 #pragma unroll
-                for (int q = 0; q < 16; ++q) res[res_swz(mo | K.joff[16 * g4 + q])] = make_float2(r[2 * q], r[2 * q + 1]);
+                    for (int q = 0; q < 16; ++q) __stcs(g + (mg | K.jg[16 * g4 + q]), make_float2(r[2 * q], r[2 * q + 1]));
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) res[res_swz(mo | K.joff[16 * g4 + q])] = make_float2(r[2 * q], r[2 * q + 1]);
+                }
             } else {
                 // lane = output real 2j + c (j = 16 q + lane / 2), columns = rows rr0 .. rr0 + 31
                 // of output half t' = g / 2 (rr0 = 32 (g % 2)); lanes 2i, 2i + 1 swap halves so
@@ -514,13 +532,15 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         tc_fence_before();
         __syncthreads();
-        for (uint32_t v = tid; v < nvec; v += kThreads) {
-            const uint32_t seg = v >> vps_log, w = v & ((1u << vps_log) - 1);
-            const uint64_t so = K.seg_lo[seg & 63] | K.seg_hi[(seg >> 6) & 63];
-            const float2 a0 = res[res_swz(2 * v)], a1 = res[res_swz(2 * v + 1)];
-            __stcs(reinterpret_cast<float4 *>(g + so) + w, make_float4(a0.x, a0.y, a1.x, a1.y));
+        if (!direct) {
+            for (uint32_t v = tid; v < nvec; v += kThreads) {
+                const uint32_t seg = v >> vps_log, w = v & ((1u << vps_log) - 1);
+                const uint64_t so = K.seg_lo[seg & 63] | K.seg_hi[(seg >> 6) & 63];
+                const float2 a0 = res[res_swz(2 * v)], a1 = res[res_swz(2 * v + 1)];
+                __stcs(reinterpret_cast<float4 *>(g + so) + w, make_float4(a0.x, a0.y, a1.x, a1.y));
+            }
+            __syncthreads();  // the operand region is rewritten by the next split
         }
-        __syncthreads();  // the operand region is rewritten by the next split
     }
     // timeout path: no copy may land after the CTA has left
     if (warp == 0)
