@@ -558,6 +558,225 @@ __global__ void __launch_bounds__(kThreads, 1)
                      : "memory");
 }
 
+
+// ---------------------------------------------------------------------------------------------
+// Pipelined BF16 x 3 kernel for 6-qubit gates whose 4 lowest row bits are the slab's 4 lowest
+// bits (the usual layout; the read-back then stores straight to HBM).  The split converts the
+// FP32 slab in place -- hi and lo BF16 parts take exactly the FP32 footprint -- so two slab
+// buffers X0, X1 and the resident E images fit shared memory (3 x 64 KiB), and two TMEM
+// accumulators let slab i's split and MMAs overlap slab i-1's read-back, while slab i+2's
+// gather is in flight:
+//   iteration i:  wait gather(i) -> split(i) in X(i&1) -> MMAs(i) into accumulator i&1
+//                 -> wait MMAs(i-1) -> read-back(i-1) to HBM
+//                 -> wait MMAs(i) (X(i&1) free) -> gather(i+2) into X(i&1)
+constexpr uint32_t kPipeX = 1u << 16;                   // one slab buffer: 64 KiB
+constexpr uint32_t kPipeOffE = 2 * kPipeX, kPipeOffCtl = 3 * kPipeX;
+
+struct TcPipeCtl {
+    unsigned long long bar[2];  // MMAs into accumulator b completed
+    uint32_t tmem;
+    uint32_t pad;
+    DevTc tc;
+    uint64_t seg_lo[64], seg_hi[64];
+    uint64_t jg[64];     // state offset (from the slab's base) of target index j
+    uint16_t joff[64];   // slab-local offset of target index j
+    uint16_t moff[128];  // slab-local offset of row m
+};
+
+__global__ void __launch_bounds__(kThreads, 1)
+    tc_pipe_kernel(float2 *__restrict__ state, const DevTc *__restrict__ d_tc,
+                   const unsigned char *__restrict__ images, uint64_t nslabs, int *status)
+{
+    constexpr uint32_t kCols = 2u * kTcK;  // two 128-column accumulators
+    constexpr uint32_t kAtom = kTcRows * 128u;
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char *base = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    TcPipeCtl &K = *reinterpret_cast<TcPipeCtl *>(base + kPipeOffCtl);
+    const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t bar0 = saddr(&K.bar[0]);
+
+    if (tid == 0) {
+        K.tc = *d_tc;
+        mbar_init(bar0, 1);
+        mbar_init(bar0 + 8u, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(&K.tmem)),
+                     "r"(kCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    {
+        // resident E images: per K atom, hi then lo (64 KiB)
+        const unsigned char *img = images + d_tc->img;
+        const uint32_t dst = saddr(base + kPipeOffE);
+        for (uint32_t v = tid; v < (4 * kAtom) / 16; v += kThreads) cp_async16(dst + 16 * v, img + 16 * v);
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = K.tmem;
+    const DevPass &P = K.tc.slab;
+    const int lo = P.lo, nhi = P.nhi;
+    for (uint32_t j = tid; j < 128; j += kThreads) {
+        const uint32_t x = j & 63, sh = (j < 64) ? 0 : 6;
+        uint64_t o = 0;
+        for (int m = 0; m < 6; ++m)
+            if ((x >> m & 1) && int(m + sh) < nhi) o |= 1ull << P.hipos[m + sh];
+        if (j < 64) K.seg_lo[x] = o; else K.seg_hi[x] = o;
+    }
+    for (uint32_t j = tid; j < 64; j += kThreads) {
+        uint32_t o = 0;
+        for (int t = 0; t < kTcTargets; ++t)
+            if (j >> t & 1) o |= 1u << K.tc.tpos[t];
+        K.joff[j] = (uint16_t)o;
+    }
+    for (uint32_t m = tid; m < 128; m += kThreads) {
+        uint32_t o = 0;
+        for (int t = 0; t < 7; ++t)
+            if (m >> t & 1) o |= 1u << K.tc.mpos[t];
+        K.moff[m] = (uint16_t)o;
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    for (uint32_t j = tid; j < 64; j += kThreads) {
+        const uint32_t x = K.joff[j];
+        K.jg[j] = K.seg_lo[(x >> lo) & 63] | K.seg_hi[(x >> (lo + 6)) & 63] | (x & ((1u << lo) - 1));
+    }
+    __syncthreads();
+
+    const int vps_log = lo - 1;  // 16-byte vectors per segment
+    const uint32_t nvec = 1u << (kTcSlabBits - 1);
+    const uint64_t nmine = uint64_t(blockIdx.x) < nslabs ? (nslabs - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    auto slab_ptr = [&](uint64_t i) -> float2 * {  // this CTA's i-th slab
+        uint64_t gb = (uint64_t(blockIdx.x) + i * gridDim.x) << lo;
+        for (int m = 0; m < nhi; ++m) {
+            const uint64_t lowm = (1ull << P.hipos[m]) - 1;
+            gb = ((gb & ~lowm) << 1) | (gb & lowm);
+        }
+        return state + gb;
+    };
+    auto issue_gather = [&](uint64_t i) {
+        const float2 *g = slab_ptr(i);
+        const uint32_t X = saddr(base + uint32_t(i & 1) * kPipeX);
+        for (uint32_t v = tid; v < nvec; v += kThreads) {
+            const uint32_t seg = v >> vps_log, w = v & ((1u << vps_log) - 1);
+            const uint64_t so = K.seg_lo[seg & 63] | K.seg_hi[(seg >> 6) & 63];
+            cp_async16(X + 16u * v, reinterpret_cast<const uint4 *>(g + so) + w);
+        }
+        cp_async_commit();
+    };
+    if (nmine > 0) issue_gather(0);
+    if (nmine > 1) issue_gather(1);
+    uint32_t ph = 0;       // bit b: parity of accumulator b's next completion
+    uint32_t pending = 0;  // bit b: a commit on bar[b] not yet waited for
+    bool failed = false;
+    auto wait_acc = [&](uint32_t b) -> bool {  // every thread; false (for all) on a timeout
+        const bool ok = mbar_wait_bounded(bar0 + 8u * b, (ph >> b) & 1u);
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) atomicExch(status, QS_ETIMEOUT);
+            return false;
+        }
+        ph ^= 1u << b;
+        pending &= ~(1u << b);
+        return true;
+    };
+    for (uint64_t i = 0; i <= nmine; ++i) {
+        if (i < nmine) {
+            // gather(i) is the older of at most two outstanding copy groups
+            if (i + 1 < nmine) cp_async_wait<1>();
+            else cp_async_wait<0>();
+            __syncthreads();
+            unsigned char *X = base + uint32_t(i & 1) * kPipeX;
+            const float2 *slab = reinterpret_cast<const float2 *>(X);
+            // split in place: thread (m, p) = (tid % 128, tid / 128) reads its 16 amplitudes,
+            // then (after every thread has read) writes its 4 hi and 4 lo 16-byte chunks
+            const uint32_t m = tid & 127u, mo = K.moff[m], c16b = (tid >> 7) * kChunksPerThread;
+            uint4 hv[kChunksPerThread], lv[kChunksPerThread];
+#pragma unroll
+            for (uint32_t c = 0; c < kChunksPerThread; ++c) {
+                __nv_bfloat162 h2[4], l2[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const float2 a = slab[mo | K.joff[(c16b + c) * 4 + q]];
+                    const __nv_bfloat16 hx = __float2bfloat16_rn(a.x), hy = __float2bfloat16_rn(a.y);
+                    h2[q] = __halves2bfloat162(hx, hy);
+                    l2[q] = __halves2bfloat162(__float2bfloat16_rn(a.x - __bfloat162float(hx)),
+                                               __float2bfloat16_rn(a.y - __bfloat162float(hy)));
+                }
+                hv[c] = *reinterpret_cast<const uint4 *>(h2);
+                lv[c] = *reinterpret_cast<const uint4 *>(l2);
+            }
+            __syncthreads();
+#pragma unroll
+            for (uint32_t c = 0; c < kChunksPerThread; ++c) {
+                const uint32_t off = op_chunk_offset(m, c16b + c);
+                *reinterpret_cast<uint4 *>(X + off) = hv[c];
+                *reinterpret_cast<uint4 *>(X + 2 * kAtom + off) = lv[c];
+            }
+            fence_proxy_async();
+            __syncthreads();
+            if (tid == 0) {
+                tc_fence_after();
+                // D_(i&1) = S_hi E_hi^T + S_hi E_lo^T + S_lo E_hi^T over 8 K-steps of 16; the E
+                // image holds per K atom its hi part, then its lo part
+                const uint32_t sx = saddr(X), se = saddr(base + kPipeOffE);
+                const uint32_t d = tmem + uint32_t(i & 1) * kTcK;
+#pragma unroll
+                for (uint32_t pr = 0; pr < 3; ++pr)
+#pragma unroll
+                    for (uint32_t ks = 0; ks < 8; ++ks) {
+                        const uint32_t atom = ks >> 2, koff = (ks & 3u) * 32u;
+                        const uint32_t a = sx + (pr == 2 ? 2 * kAtom : 0u) + atom * kAtom + koff;
+                        const uint32_t b = se + atom * 2 * kAtom + (pr == 1 ? kAtom : 0u) + koff;
+                        mma_bf16(d, smem_desc(a), smem_desc(b), kIdescBf16, (pr | ks) ? 1u : 0u);
+                    }
+                mma_commit(bar0 + 8u * uint32_t(i & 1));
+            }
+            pending |= 1u << uint32_t(i & 1);
+        }
+        if (i >= 1) {
+            // read-back of slab i - 1 straight to HBM: warp w reads TMEM lane quarter w % 4
+            // (32 rows, = two whole 128-byte segments per target value), columns 32 (w / 4) ..
+            const uint32_t b = uint32_t((i - 1) & 1);
+            if ((pending >> b & 1) && !wait_acc(b)) {
+                failed = true;
+                break;
+            }
+            tc_fence_after();
+            float2 *g = slab_ptr(i - 1);
+            const uint32_t q4 = warp & 3u, g4 = warp >> 2;
+            float r[32];
+            tmem_ld32(tmem + b * kTcK + ((q4 * 32u) << 16) + 32u * g4, r);
+            const uint32_t mo = K.moff[q4 * 32 + lane];
+            const uint64_t mg = K.seg_lo[(mo >> lo) & 63] | K.seg_hi[(mo >> (lo + 6)) & 63] | (mo & ((1u << lo) - 1));
+#pragma unroll
+            for (int q = 0; q < 16; ++q) __stcs(g + (mg | K.jg[16 * g4 + q]), make_float2(r[2 * q], r[2 * q + 1]));
+        }
+        if (i + 2 < nmine) {
+            // slab i's buffer is free once its MMAs have completed: gather slab i + 2 into it
+            if (!wait_acc(uint32_t(i & 1))) {
+                failed = true;
+                break;
+            }
+            issue_gather(i + 2);
+        }
+        tc_fence_before();
+        __syncthreads();  // accumulator (i - 1) & 1 has been read before MMAs(i + 1) overwrite it
+    }
+    // timeout path: copies and MMAs in flight finish before the CTA leaves
+    cp_async_wait_all();
+    for (uint32_t b = 0; b < 2; ++b)
+        if (failed && (pending >> b & 1)) mbar_wait_bounded(bar0 + 8u * b, (ph >> b) & 1u);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCols)
+                     : "memory");
+}
+
 }  // namespace
 
 size_t tc_image_bytes(int mode, int width)
@@ -590,6 +809,30 @@ int launch_tc_t(const LaunchCtx &c, const DevTc *d_tc, const void *d_images, cha
     }
     return QS_OK;
 }
+
+int launch_tc_pipe(const LaunchCtx &c, const DevTc *d_tc, const void *d_images, char *err, size_t errlen)
+{
+    const size_t smem = kPipeOffCtl + sizeof(TcPipeCtl) + 1024;
+    static int attr_dev = -1;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (attr_dev != dev) {
+        cudaFuncSetAttribute(tc_pipe_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attr_dev = dev;
+    }
+    const uint64_t nslabs = 1ull << (c.n - kTcSlabBits);
+    uint64_t grid = uint64_t(num_sms());
+    if (grid > nslabs) grid = nslabs;
+    tc_pipe_kernel<<<(unsigned)grid, kThreads, smem, (cudaStream_t)c.stream>>>(
+        reinterpret_cast<float2 *>(c.amp), d_tc, reinterpret_cast<const unsigned char *>(d_images), nslabs,
+        device_status_ptr());
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        snprintf(err, errlen, "tensor-core launch failed: %s", cudaGetErrorString(e));
+        return QS_ECUDA;
+    }
+    return QS_OK;
+}
 }  // namespace
 
 int launch_tc(const LaunchCtx &c, const DevTc *d_tc, const DevTc &h, const void *d_images, char *err,
@@ -604,6 +847,11 @@ int launch_tc(const LaunchCtx &c, const DevTc *d_tc, const DevTc &h, const void 
         return QS_EINVAL;
     }
     const bool w7 = h.width == 7;
+    // 6-qubit BF16 gates in the usual layout (the slab's 4 lowest bits are row bits 0-3): the
+    // pipelined kernel
+    if (h.mode == QS_TC_BF16X3 && !w7 && h.slab.lo >= 4 && h.mpos[0] == 0 && h.mpos[1] == 1 && h.mpos[2] == 2 &&
+        h.mpos[3] == 3)
+        return launch_tc_pipe(c, d_tc, d_images, err, errlen);
     if (h.mode == QS_TC_BF16X3)
         return w7 ? launch_tc_t<QS_TC_BF16X3, 4>(c, d_tc, d_images, err, errlen)
                   : launch_tc_t<QS_TC_BF16X3, 1>(c, d_tc, d_images, err, errlen);

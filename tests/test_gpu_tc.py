@@ -169,3 +169,16 @@ def test_seven_and_six_qubit_steps_in_one_plan():
     got, st = run_tc(n, gates, init, qs.QS_TC_BF16X3, 7)
     assert infidelity(want, got) <= 1e-6
     assert np.max(np.abs(got - want)) <= 1e-5
+
+
+@pytest.mark.parametrize("n", [20, 21, 22])
+def test_pipelined_slab_counts(n):
+    """BF16x3 6-qubit gates in the usual layout run a two-slab pipeline per CTA; 20, 21 and 22
+    qubits give CTAs 0-1, 1-2 and 3-4 slabs (152 CTAs), the pipeline's short cases."""
+    gates = W.layered(n, 4, 1005)
+    init = rand_state(n, 11)
+    want = oracle.apply_circuit(n, gates, init.copy())
+    got, st = run_tc(n, gates, init)
+    assert st["tc_gates"] > 0
+    assert infidelity(want, got) <= 1e-6
+    assert np.max(np.abs(got - want)) <= 1e-5
