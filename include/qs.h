@@ -121,8 +121,9 @@ typedef struct {
                             (folded into the stage's diagonal tables).  0 = on (the default),
                             1 = off */
     int32_t merge_bits;  /* register stages: most condition bits (slab or outer qubits) one merged
-                            diagonal table may read besides the register bits; 0 = automatic (6),
-                            at most 10 (tables of 2^(stage_bits + merge_bits) entries) */
+                            diagonal table may read besides the register bits; 0 = automatic (10
+                            for complex128 stages in FP64, else 6), at most 10 (tables of
+                            2^(stage_bits + merge_bits) entries) */
     int32_t arith;       /* qs_arith: arithmetic of complex128 register stages */
     int32_t reserved[3];
 } qs_options;

@@ -35,7 +35,7 @@ def candidate_options(dtype: int, n: int):
         for fw, force in FUSES:
             for sb in range(max(bmax - 2, 6), bmax + 1):
                 for rb in (rbmax - 1, rbmax):
-                    for mb in (0, 8, 10):
+                    for mb in (6, 8, 10):
                         out.append(dict(fuse_width=fw, fuse_force=force, slab_bits=sb, stage_bits=rb, euler=eu,
                                         merge_bits=mb))
     return out

@@ -172,7 +172,7 @@ int learned_choose(const std::vector<CGate> &gates, int n, qs_dtype dt, const qs
     };
     const Fuse fuses[] = {{1, 0}, {2, 0}, {3, 1}, {4, 1}, {5, 1}};
     std::vector<qs_options> cand;
-    const int merges[] = {0, 8, 10};  // stage-table condition bits: the default 6, 8 or 10
+    const int merges[] = {6, 8, 10};  // stage-table condition bits
     for (int eu = 1; eu <= 2; ++eu)
         for (const Fuse &fz : fuses)
             for (int sb = std::max(bmax - 2, 6); sb <= bmax; ++sb)

@@ -616,11 +616,15 @@ bool controlled_phase(const CGate &g, cd &phase)
 // includes slab bits outside the registers or physical bits outside the slab joins too: those
 // bits are constant for a thread's group, so they index the table (up to kMergeCondBits of them
 // per table).  Diagonal tables that already read such bits stay where they are.
-constexpr int kMergeCondBitsDefault = 6;  // condition bits of one merged table (2^(RB + 6) entries)
+// Condition bits of one merged table when qs_options.merge_bits is 0: 10 for complex128 stages
+// in FP64, whose time is FP64 multiplies (QFT-32: 2.23 s with 6 bits, 1.98 s with 10; layered
+// circuits within 0.3 %), else 6 (complex64 and double-float stages are slightly slower with
+// the larger tables).
+int default_merge_bits(const Plan &plan) { return plan.dt == QS_C128 && plan.opt.arith == QS_ARITH_FP64 ? 10 : 6; }
 
 void merge_stage_diagonals(Plan &plan, int s0, int RB, Coefs &cf)
 {
-    const int kMergeCondBits = plan.opt.merge_bits > 0 ? std::min(plan.opt.merge_bits, 10) : kMergeCondBitsDefault;
+    const int kMergeCondBits = plan.opt.merge_bits > 0 ? std::min(plan.opt.merge_bits, 10) : default_merge_bits(plan);
     const int E = 1 << RB;
     std::vector<DevSub> in(plan.subs.begin() + s0, plan.subs.end());
     const int ns = (int)in.size();

@@ -68,7 +68,7 @@ def test_candidate_grid_matches_planner_limits():
         assert len(grid) == 2 * 5 * 3 * 2 * 3
         assert {o["slab_bits"] for o in grid} == {bmax - 2, bmax - 1, bmax}
         assert {o["stage_bits"] for o in grid} == {rb - 1, rb}
-        assert {o["merge_bits"] for o in grid} == {0, 8, 10}
+        assert {o["merge_bits"] for o in grid} == {6, 8, 10}
         for o in grid:
             p = qs.qs_fuse(W.qft(18), 18, qs.options(dtype=dt, **o))
             assert qs.qs_plan_info_get(p)["slab_bits"] <= o["slab_bits"]
