@@ -15,9 +15,12 @@
 // 128-byte-swizzled K-major operand layout -> 24 tcgen05.mma (3 products x 8 K-steps of 16)
 // issued by one thread into a 128-lane x 128-column FP32 accumulator in TMEM ->
 // tcgen05.commit to an mbarrier -> tcgen05.ld of the accumulator by the 16 warps (four per TMEM
-// lane quarter) -> into the (now free) operand region -> 16-byte stores.  The next slab's
-// gather is issued as soon as the split has read the slab buffer, so it overlaps the MMAs, the
-// accumulator read-back and the stores.  Every mbarrier wait is bounded; on expiry the CTA
+// lane quarter) -> straight to HBM when the slab's 4 lowest bits are row bits (one read-back
+// instruction then covers two whole 128-byte segments), else through the (now free), swizzled
+// operand region and 16-byte stores.  The next slab's gather is issued as soon as the split has
+// read the slab buffer, so it overlaps the MMAs, the accumulator read-back and the stores.
+// BF16 x 3 6-qubit gates in that usual layout run in tc_pipe_kernel (below), which keeps two
+// slabs in flight per CTA.  Every mbarrier wait is bounded; on expiry the CTA
 // records QS_ETIMEOUT, waits (bounded) for its copies in flight, releases its tensor memory
 // and exits.
 //
@@ -47,14 +50,16 @@ constexpr uint32_t kChunksPerThread = 16 * kTcRows / kThreads;  // 16-byte opera
 // TF32 operand (128 x 64 x 4 B): 32 KiB either way.
 constexpr uint32_t kOpBytes = kTcRows * kTcK * 2;
 constexpr uint32_t kSlabBytes = (1u << kTcSlabBits) * 8;
+// shared memory: FP32 slab buffer | slab operand hi | lo | E region (64 KiB: the resident image,
+// one K half's image or two stream buffers) | control block
 constexpr uint32_t kOffAhi = kSlabBytes, kOffAlo = kOffAhi + kOpBytes, kOffBhi = kOffAlo + kOpBytes,
-                   kOffBlo = kOffBhi + kOpBytes, kOffCtl = kOffBlo + kOpBytes;
+                   kOffCtl = kOffBhi + 2 * kOpBytes;
 constexpr uint32_t kWaitLimit = 1u << 24;
 
 struct TcCtl {
     unsigned long long mbar;      // all MMAs issued so far completed (every thread waits)
-    unsigned long long full[2];   // E chunk buffer b: bulk copies landed (thread 0 waits)
-    unsigned long long mdone[2];  // E chunk buffer b: its MMAs completed (thread 0 waits)
+    unsigned long long full[2];   // E buffer b: bulk copies landed (warp 0 waits)
+    unsigned long long mdone[2];  // E buffer b: its MMAs completed (warp 0 waits)
     uint32_t tmem;
     uint32_t pad;
     DevTc tc;
