@@ -191,6 +191,21 @@ __device__ __forceinline__ void sub_g1r(C (&v)[1 << RB], const C *__restrict__ M
 template <typename C, int RB, int J, int K, typename R>
 __device__ __forceinline__ void sub_g1n(C (&v)[1 << RB], R x, R y)
 {
+    if constexpr (sizeof(C) == 8 && K < 2) {
+        // complex64, unit diagonal: b' first, then a' from b' (K = 0: a' = (1 - xy) a + x b';
+        // K = 1: a' = (1 + xy) a - x b'), so both results overwrite their inputs and no copy
+        // through a temporary is needed; |x|, |y| <= 1, so the coefficients stay within 2
+        const R c = K == 0 ? fmaf(-x, y, R(1)) : fmaf(x, y, R(1));
+        const R xs = K == 0 ? x : -x;
+#pragma unroll
+        for (int e = 0; e < (1 << RB); ++e) {
+            if (e & (1 << J)) continue;
+            const int e1 = e | (1 << J);
+            v[e1] = K == 0 ? rfma(y, v[e], v[e1]) : rfms(y, v[e], v[e1]);
+            v[e] = rfma(xs, v[e1], rmul(c, v[e]));
+        }
+        return;
+    }
 #pragma unroll
     for (int e = 0; e < (1 << RB); ++e) {
         if (e & (1 << J)) continue;
