@@ -81,7 +81,7 @@ typedef struct {
 } qs_pauli_term;
 
 typedef enum { QS_PLANNER_GREEDY = 0, QS_PLANNER_LEARNED = 1 } qs_planner;
-/* Tensor-core modes for fused 6-qubit gates on complex64 states: split precision with three
+/* Tensor-core modes for fused 6- and 7-qubit gates on complex64 states: split precision with three
  * products (hi*hi + hi*lo + lo*hi) and FP32 accumulation, parts in TF32 (about 22 significant
  * bits for hi + lo) or BF16 (about 16 bits).  Not in the paper: a GB300 form of its dense gates. */
 typedef enum { QS_TC_OFF = 0, QS_TC_TF32X3 = 1, QS_TC_BF16X3 = 2 } qs_tc_mode;
@@ -103,7 +103,9 @@ typedef struct {
                             low-block slabs plus explicit remap passes (Alg. 4) */
     int32_t planner;     /* qs_planner */
     int32_t tc;          /* qs_tc_mode: tensor-core path for wide fused gates (complex64 only) */
-    int32_t tc_width;    /* qubits per tensor-core fused gate: 6 or 7 */
+    int32_t tc_width;    /* widest tensor-core fused gate: 6 (0 = 6) or 7; blocks of 4-6 qubits
+                            are padded to 6, blocks of 7 run as four 64x64 products; any other
+                            value: QS_EUNSUPPORTED */
     int32_t graph;       /* 1 = replay the plan's launches from a captured CUDA graph */
     int32_t diag_bits;   /* widest fused diagonal table (qubits), 0 = automatic */
     int32_t dtype;       /* qs_dtype the plan's cost model targets (qs_apply_circuit sets it
