@@ -65,6 +65,22 @@ def op_gate(kind, t, c, m):
     raise ValueError(kind)
 
 
+ORACLE_MAX_DIAG = 12  # widest DIAG gate the oracle takes
+
+
+def apply_wide_diag(state, n, t, c, m):
+    """A diagonal wider than the oracle's DIAG gate, by its definition (Eq. 3 with a diagonal
+    matrix): amplitude x is multiplied by m[sum_j bit(x, t_j) 2^j] where every control bit is 1."""
+    x = np.arange(1 << n, dtype=np.int64)
+    idx = np.zeros_like(x)
+    for j, q in enumerate(t):
+        idx |= ((x >> q) & 1) << j
+    on = np.ones(1 << n, dtype=bool)
+    for q in c:
+        on &= ((x >> q) & 1) == 1
+    state[on] *= m[idx[on]]
+
+
 def replay(text, state):
     """Execute the listing on `state` (complex128, physical order) in place; returns layout."""
     n, items, layout = parse_dump(text)
@@ -87,7 +103,10 @@ def replay(text, state):
                 # non-diagonal targets must be slab-resident
                 assert set(t) <= cur_slab, (kind, t, sorted(cur_slab))
             stats["ops"] += 1
-            oracle.apply_circuit(n, [op_gate(kind, t, c, m)], state)
+            if kind == "DIAG" and len(t) > ORACLE_MAX_DIAG:
+                apply_wide_diag(state, n, t, c, m)
+            else:
+                oracle.apply_circuit(n, [op_gate(kind, t, c, m)], state)
     return layout, stats
 
 

@@ -351,3 +351,26 @@ def test_identity_products_are_dropped():
     phase = [Gate("DIAG", (1,), (), (), np.array([1j, 1j]))]
     info, stats = check_plan(phase, n, qs.options(dtype=qs.QS_C128))
     assert stats["ops"] == 1
+
+
+@pytest.mark.parametrize("dtype,arith,widest", [(qs.QS_C128, qs.QS_ARITH_FP64, 4 + 10),
+                                                (qs.QS_C128, qs.QS_ARITH_DF, 4 + 6),
+                                                (qs.QS_C64, qs.QS_ARITH_FP64, 5 + 6)])
+def test_stage_table_condition_bits_default_by_arithmetic(dtype, arith, widest):
+    """merge_bits = 0: merged stage tables read up to 10 condition bits besides the register bits
+    for complex128 stages in FP64 (whose time is FP64 multiplies), 6 otherwise; the replayed
+    plan still equals the oracle, and an explicit merge_bits overrides the default."""
+    n = 16
+    g = W.qft(n)
+    info, stats = check_plan(g, n, qs.options(dtype=dtype, arith=arith), seed=5)
+    p = qs.qs_fuse(g, n, qs.options(dtype=dtype, arith=arith))
+    q = qs.qs_fuse(g, n, qs.options(dtype=dtype, arith=arith, merge_bits=2))
+    try:
+        widths = [int(l.split()[2]) for l in qs.qs_plan_dump(p).splitlines() if l.startswith("OP DIAG")]
+        narrow = [int(l.split()[2]) for l in qs.qs_plan_dump(q).splitlines() if l.startswith("OP DIAG")]
+    finally:
+        qs.qs_plan_destroy(p)
+        qs.qs_plan_destroy(q)
+    rb = 5 if dtype == qs.QS_C64 else 4  # register bits of a stage
+    assert max(widths) == widest
+    assert max(narrow) <= rb + 2
